@@ -1,0 +1,224 @@
+"""Seeded synthetic inputs for sparse FastTucker workloads.
+
+This module only draws random data: coordinates (uniform or Zipf-skewed per
+mode), planted factor and core matrices, noise, train/test splits and the
+rating map for integer-valued tensors.  It holds none of the method's
+arithmetic: the values of a planted tensor are the planted model's
+predictions, and those are computed by whoever consumes the draw (the CPU
+oracle in the tests, the library's own predict call in the benchmark).
+
+Workload shapes follow the paper's experiments (Sec. 5.1, Table "Datasets"):
+a Netflix-shaped 3-order tensor (480,189 x 17,770 x 2,182 users x movies x
+days, about 1e8 ratings in 1..5), a Yahoo!Music-shaped tensor, and the
+synthetic order-3..10 tensors.  The real datasets are not available, so
+skewed (Zipf) index popularity stands in for their structure.
+
+Everything is driven by torch generators so that the large draws run on the
+device; the small ones run on the CPU with the same code.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+
+import torch
+
+
+def generator(seed: int, device="cpu") -> torch.Generator:
+    g = torch.Generator(device=device)
+    g.manual_seed(int(seed))
+    return g
+
+
+def zipf_cdf(I: int, s: float, device="cpu") -> torch.Tensor:
+    """Cumulative distribution of a Zipf law truncated to ranks 1..I (float64)."""
+    k = torch.arange(1, I + 1, dtype=torch.float64, device=device)
+    p = k.pow(-float(s))
+    c = torch.cumsum(p, 0)
+    return c / c[-1]
+
+
+def draw_mode_indices(gen: torch.Generator, I: int, nnz: int, dist: str = "uniform",
+                      s: float = 1.1, device="cpu") -> torch.Tensor:
+    """Draw nnz row indices in [0, I) for one mode (int64).
+
+    ``uniform``: i.i.d. uniform rows.  ``zipf``: the rank of each draw follows
+    a truncated Zipf(s) law (inverse CDF on the precomputed table) and ranks
+    are mapped to row ids through a seeded random permutation, so that hot rows
+    are scattered over the matrix rather than packed at its top.
+    """
+    if dist == "uniform":
+        return torch.randint(0, I, (nnz,), generator=gen, device=device, dtype=torch.int64)
+    if dist != "zipf":
+        raise ValueError(f"unknown index distribution {dist!r}")
+    cdf = zipf_cdf(I, s, device=device)
+    u = torch.rand(nnz, generator=gen, device=device, dtype=torch.float64)
+    rank = torch.searchsorted(cdf, u).clamp_(max=I - 1)
+    ids = torch.randperm(I, generator=gen, device=device)
+    return ids[rank]
+
+
+def dedup_coords(idx: torch.Tensor) -> torch.Tensor:
+    """Drop repeated coordinates, keeping the first occurrence of each.
+
+    idx: [N, nnz] int64.  The surviving columns keep their original order
+    (which is random, so the result is still a random sample order).
+    Uses N stable sorts (lexicographic order by mode N, ..., 1) so that no
+    linearised key can overflow for large mode sizes.
+    """
+    N, nnz = idx.shape
+    if nnz == 0:
+        return idx
+    order = torch.arange(nnz, device=idx.device)
+    for n in reversed(range(N)):
+        _, o = torch.sort(idx[n, order], stable=True)
+        order = order[o]
+    srt = idx[:, order]
+    same = torch.ones(nnz, dtype=torch.bool, device=idx.device)
+    same[0] = False
+    same[1:] = (srt[:, 1:] == srt[:, :-1]).all(dim=0)
+    keep_pos = order[~same]
+    keep_pos, _ = torch.sort(keep_pos)
+    return idx[:, keep_pos]
+
+
+def normal_matrices(gen: torch.Generator, shapes, std: float, device="cpu",
+                    dtype=torch.float32):
+    """One N(0, std^2) matrix per shape (std is the standard deviation)."""
+    return [
+        (torch.randn(tuple(sh), generator=gen, device=device, dtype=torch.float64) * std).to(dtype)
+        for sh in shapes
+    ]
+
+
+def uniform_matrices(gen: torch.Generator, shapes, hi: float, device="cpu",
+                     dtype=torch.float32):
+    return [
+        (torch.rand(tuple(sh), generator=gen, device=device, dtype=torch.float64) * hi).to(dtype)
+        for sh in shapes
+    ]
+
+
+def rating_scale_init(J: int, R: int, N: int, mean_value: float) -> float:
+    """Upper end s of a U(0, s) initialisation whose expected prediction is
+    about ``mean_value`` for ratings-valued tensors: each of the N factor/core
+    products averages J*s^2/4 and the prediction sums R products of N of them."""
+    per_mode = (mean_value / R) ** (1.0 / N)
+    return math.sqrt(4.0 * per_mode / J)
+
+
+def to_ratings(pred: torch.Tensor, centre: float = 3.0, spread: float = 1.1,
+               lo: float = 1.0, hi: float = 5.0) -> torch.Tensor:
+    """Map planted predictions to integer ratings lo..hi: standardise, scale,
+    round, clip (float32 output)."""
+    p = pred.to(torch.float64)
+    z = (p - p.mean()) / p.std().clamp_min(1e-30)
+    return torch.clamp(torch.round(centre + spread * z), lo, hi).to(torch.float32)
+
+
+def split_train_test(gen: torch.Generator, nnz: int, test_frac: float, device="cpu"):
+    """Random split of positions 0..nnz-1 (both parts keep a random order)."""
+    perm = torch.randperm(nnz, generator=gen, device=device)
+    n_test = int(round(nnz * test_frac))
+    return perm[n_test:], perm[:n_test]
+
+
+@dataclass
+class Workload:
+    """A named synthetic tensor recipe (sizes, index law, planted model)."""
+    name: str
+    I: tuple
+    nnz: int
+    J: tuple
+    R: int
+    dist: str = "uniform"
+    zipf_s: float = 1.1
+    planted_std: float | None = None    # None: 1/sqrt(J)
+    noise_std: float = 0.0
+    ratings: bool = False
+    test_frac: float = 0.1
+    seed: int = 0
+    extra: dict = field(default_factory=dict)
+
+    @property
+    def N(self) -> int:
+        return len(self.I)
+
+
+# Named recipes.  Mode sizes of the Netflix-shaped tensor follow the paper's
+# dataset table (Sec. 5.1); the Zipf skew stands in for the popularity
+# structure of real ratings.
+WORKLOADS = {
+    "planted_uniform_1e5": Workload(
+        name="planted_uniform_1e5", I=(1000, 1000, 1000), nnz=100_000, J=(4, 4, 4), R=4,
+        dist="uniform", planted_std=0.5, noise_std=0.1),
+    "netflix_shaped_zipf_1e8": Workload(
+        name="netflix_shaped_zipf_1e8", I=(480_000, 18_000, 2_200), nnz=100_000_000,
+        J=(16, 16, 16), R=16, dist="zipf", zipf_s=1.1, planted_std=0.25, ratings=True),
+    "order4_zipf_2e8": Workload(
+        name="order4_zipf_2e8", I=(1_000_000, 1_000_000, 100_000, 1_000), nnz=200_000_000,
+        J=(32, 32, 32, 32), R=32, dist="zipf", zipf_s=1.05, noise_std=0.05),
+}
+
+
+@dataclass
+class Draw:
+    """The random part of a workload: coordinates, planted model, noise, split."""
+    idx: torch.Tensor            # [N, nnz] int32, deduplicated, random order
+    planted_A: list
+    planted_B: list
+    noise: torch.Tensor          # [nnz] float32 (zeros when noise_std == 0)
+    train: torch.Tensor          # positions of the training nonzeros
+    test: torch.Tensor           # positions of the test nonzeros
+
+
+def draw_workload(w: Workload, device="cpu", nnz: int | None = None) -> Draw:
+    """Draw coordinates, the planted model, noise and the split of ``w``.
+
+    ``nnz`` overrides the coordinate count (a prefix-sized sample of the
+    same recipe)."""
+    gen = generator(w.seed, device)
+    n_coords = int(w.nnz if nnz is None else nnz)
+    cols = [draw_mode_indices(gen, I, n_coords, w.dist, w.zipf_s, device) for I in w.I]
+    idx = dedup_coords(torch.stack(cols))
+    del cols
+    nnz_u = idx.shape[1]
+    std_of = (lambda J: w.planted_std) if w.planted_std is not None else (lambda J: 1.0 / math.sqrt(J))
+    A = [normal_matrices(gen, [(I, J)], std_of(J), device)[0] for I, J in zip(w.I, w.J)]
+    B = [normal_matrices(gen, [(J, w.R)], std_of(J), device)[0] for J in w.J]
+    if w.noise_std > 0:
+        noise = (torch.randn(nnz_u, generator=gen, device=device, dtype=torch.float64)
+                 * w.noise_std).to(torch.float32)
+    else:
+        noise = torch.zeros(nnz_u, dtype=torch.float32, device=device)
+    train, test = split_train_test(gen, nnz_u, w.test_frac, device)
+    return Draw(idx=idx.to(torch.int32), planted_A=A, planted_B=B, noise=noise,
+                train=train, test=test)
+
+
+def initial_factors(w: Workload, device="cpu", mean_value: float | None = None, seed_offset: int = 1):
+    """Starting point of training: N(0, 1/sqrt(J)) for planted real-valued
+    tensors, U(0, s) sized to the mean rating for ratings tensors."""
+    gen = generator(w.seed + seed_offset, device)
+    if w.ratings:
+        hi = rating_scale_init(max(w.J), w.R, w.N, 3.0 if mean_value is None else mean_value)
+        A = [uniform_matrices(gen, [(I, J)], hi, device)[0] for I, J in zip(w.I, w.J)]
+        B = [uniform_matrices(gen, [(J, w.R)], hi, device)[0] for J in w.J]
+    else:
+        A = [normal_matrices(gen, [(I, J)], 1.0 / math.sqrt(J), device)[0] for I, J in zip(w.I, w.J)]
+        B = [normal_matrices(gen, [(J, w.R)], 1.0 / math.sqrt(J), device)[0] for J in w.J]
+    return A, B
+
+
+def random_problem(seed: int, I, J, R, nnz, device="cpu", std=0.5, value_std=1.0):
+    """A small unstructured problem for parity tests: uniform coordinates
+    (duplicates allowed), N(0, std^2) factors and cores, N(0, value_std^2)
+    values."""
+    gen = generator(seed, device)
+    N = len(I)
+    idx = torch.stack([torch.randint(0, int(In), (nnz,), generator=gen, device=device)
+                       for In in I]).to(torch.int32)
+    A = [normal_matrices(gen, [(In, Jn)], std, device)[0] for In, Jn in zip(I, J)]
+    B = [normal_matrices(gen, [(Jn, R)], std, device)[0] for Jn in J]
+    x = (torch.randn(nnz, generator=gen, device=device, dtype=torch.float64) * value_std).to(torch.float32)
+    return idx, x, A, B
