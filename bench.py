@@ -1,0 +1,384 @@
+#!/usr/bin/env python3
+"""Throughput of the FastTuckerPlus SGD epoch on one GB300 (or N replicas).
+
+A step is one pass of the whole hot path over the training nonzeros of the
+Netflix-shaped synthetic tensor (N = 3, I = 480000 x 18000 x 2200, 1e8 Zipf
+coordinates, J = R = 16, 90/10 split): the factor phase, the core phase
+(gradient + finalize) and the test-set RMSE/MAE.  The metric is
+nonzero-updates per second = |Omega_train| / step time.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp32|tf32|bf16]
+  python bench.py --impl reference ...   # the FP64 CPU oracle on the host
+
+Prints one JSON line (rank 0).  Under torchrun every rank trains its own
+replica (no data-path collective) and the value is the sum over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import torch
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2404_10087_gb300 import ft, synth  # noqa: E402
+
+METRIC = "SGD nonzero-updates/sec (factor+core) at J=R=16; time-to-RMSE vs plain FP32"
+UNIT = "nnz-updates/s"
+WORKLOAD = "netflix_shaped_zipf_1e8"
+LR = 0.01
+LAM = 0.01
+FALLBACK_HBM_GBS = 6800.0
+
+
+def algorithmic_bytes_factor(N, J):
+    """Per nonzero: N int32 coordinates + one float32 value read, N factor rows
+    read and written (float32)."""
+    return 4 * N + 4 + 8 * 4 * sum(J)
+
+
+def peak_hbm():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def kernel_digest():
+    h = hashlib.sha256()
+    for name in ("ft_device.cuh",):
+        with open(os.path.join(ROOT, "paper_2404_10087_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(precision):
+    """DRAM bytes per factor launch from the committed ncu summary, if it was
+    taken on the current kernel source; else None."""
+    p = os.path.join(ROOT, "profiles", "ncu_factor_netflix_zipf.md")
+    if not os.path.exists(p):
+        return None
+    text = open(p).read()
+    m = re.search(r"kernel_source_sha256_16:\s*([0-9a-f]+)", text)
+    if not m or m.group(1) != kernel_digest():
+        return None
+    m = re.search(rf"traffic_bytes_per_launch_{precision}:\s*([0-9.eE+]+)", text)
+    return float(m.group(1)) if m else None
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+        return False
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def make_workload(device, nnz=None):
+    """Draw the synthetic tensor on `device`; planted values are computed by the
+    library's own predict call, then mapped to integer ratings 1..5."""
+    w = synth.WORKLOADS[WORKLOAD]
+    d = synth.draw_workload(w, device=device, nnz=nnz)
+    N = w.N
+    allidx = [d.idx[n].contiguous() for n in range(N)]
+    zeros = torch.zeros(d.idx.shape[1], dtype=torch.float32, device=device)
+    pm = ft.FastTuckerPlus(allidx, zeros, [a.contiguous() for a in d.planted_A],
+                           [b.contiguous() for b in d.planted_B])
+    pred = pm.predict(allidx)
+    pm.close()
+    del zeros
+    vals = synth.to_ratings(pred)
+    del pred
+    tr, te = d.train, d.test
+    train_idx = [d.idx[n, tr].contiguous() for n in range(N)]
+    test_idx = [d.idx[n, te].contiguous() for n in range(N)]
+    train_x = vals[tr].contiguous()
+    test_x = vals[te].contiguous()
+    A, B = synth.initial_factors(w, device=device, mean_value=float(train_x.double().mean()))
+    return w, train_idx, train_x, test_idx, test_x, A, B
+
+
+def run_ours(args, rank, world, local_rank):
+    dev = torch.device(f"cuda:{local_rank}")
+    torch.cuda.set_device(dev)
+    ft.load()
+    w, tri, trx, tei, tex, A, B = make_workload(dev)
+    N, J, R = w.N, list(w.J), w.R
+    nnz_train, nnz_test = int(trx.numel()), int(tex.numel())
+    stream = torch.cuda.current_stream(dev)
+    m = ft.FastTuckerPlus(tri, trx, A, B, precision=args.precision, scatter="hogwild")
+
+    ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
+
+    def step(record=None):
+        e0, e1, e2, e3 = (ev(), ev(), ev(), ev()) if record is not None else (None,) * 4
+        if record is not None:
+            e0.record(stream)
+        m.epoch_factors(LR, LAM)
+        if record is not None:
+            e1.record(stream)
+        m.epoch_core(LR, LAM)
+        if record is not None:
+            e2.record(stream)
+        r = m.rmse(tei, tex)  # synchronises: the step's result reaches the host
+        if record is not None:
+            e3.record(stream)
+            record.append((e0, e1, e2, e3))
+        return r
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    launches0 = m.launches
+    rec = []
+    with ClockSampler(local_rank) as clk:
+        torch.cuda.synchronize()
+        t0 = ev()
+        t1 = ev()
+        t0.record(stream)
+        for _ in range(args.steps):
+            last = step(rec)
+        t1.record(stream)
+        torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    total_ms = t0.elapsed_time(t1)
+    launches = m.launches - launches0
+    f_ms = [a.elapsed_time(b) for a, b, _, _ in rec]
+    c_ms = [b.elapsed_time(c) for _, b, c, _ in rec]
+    r_ms = [c.elapsed_time(d) for _, _, c, d in rec]
+
+    # end to end through the C ABI with host buffers: every step copies the
+    # training COO from pinned host memory and reads the RMSE back
+    host_idx = [t.cpu().pin_memory() for t in tri]
+    host_x = trx.cpu().pin_memory()
+    h2d = sum(t.numel() * t.element_size() for t in host_idx) + host_x.numel() * 4
+    e2e_steps = max(1, min(args.steps, 5))
+    torch.cuda.synchronize()
+    te0, te1 = ev(), ev()
+    te0.record(stream)
+    for _ in range(e2e_steps):
+        for dst, src in zip(tri, host_idx):
+            dst.copy_(src, non_blocking=True)
+        trx.copy_(host_x, non_blocking=True)
+        step()
+    te1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = te0.elapsed_time(te1) / e2e_steps
+
+    times = torch.tensor([total_ms, e2e_ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        torch.distributed.all_reduce(times, op=torch.distributed.ReduceOp.MAX)
+    total_ms, e2e_ms = float(times[0]), float(times[1])
+    ms_per_step = total_ms / args.steps
+    value = world * nnz_train / (ms_per_step / 1e3)
+    if rank != 0:
+        return None
+
+    per_nnz = algorithmic_bytes_factor(N, J)
+    fac_ms = statistics.mean(f_ms)
+    achieved = per_nnz * nnz_train / (fac_ms / 1e3) / 1e9
+    peak, peak_kind = peak_hbm()
+    traffic = recorded_traffic(args.precision)
+    clocks = clk.summary()
+    out = {
+        "metric": METRIC,
+        "value": value,
+        "unit": UNIT,
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": ms_per_step,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": {"fp32": "f32", "tf32": "tf32", "bf16": "bf16"}[args.precision],
+        "data": "synthetic (seeded Zipf coordinates, planted-model ratings; Netflix-shaped)",
+        "config": {
+            "workload": WORKLOAD, "N": N, "I": list(w.I), "J": J, "R": R,
+            "nnz_train": nnz_train, "nnz_test": nnz_test, "precision": args.precision,
+            "scatter": "hogwild", "lr": LR, "lambda": LAM,
+            "parallelism": "replicas" if world > 1 else "single",
+            "l2": "inputs larger than L2 (training COO stream 1.2 GB per epoch)",
+        },
+        "phases_ms": {"factor": statistics.median(f_ms), "core": statistics.median(c_ms),
+                      "rmse": statistics.median(r_ms)},
+        "test_rmse": last[0],
+        "roofline": {
+            "bound": "hbm", "kernel": "k_factor", "achieved": achieved, "peak": peak,
+            "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
+            "traffic": traffic, "bytes_per_nnz": per_nnz, "nnz_per_launch": nnz_train,
+            "launch_ms": fac_ms,
+        },
+        "e2e": {"value": world * nnz_train / (e2e_ms / 1e3), "unit": UNIT,
+                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": 24},
+        "gpu_launches": int(launches),
+        "clocks": clocks,
+    }
+    if not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(args.cpu_sample)
+    return out
+
+
+def oracle_sample(nnz_sample):
+    """A bounded sample of the workload for the CPU oracle: the same recipe
+    drawn at nnz_sample coordinates on the host, planted values by the oracle."""
+    import numpy as np
+    import oracle
+    w = synth.WORKLOADS[WORKLOAD]
+    d = synth.draw_workload(w, device="cpu", nnz=nnz_sample)
+    pred = oracle.predict([a.double().numpy() for a in d.planted_A],
+                          [b.double().numpy() for b in d.planted_B], d.idx.numpy(),
+                          nthreads=oracle.default_threads())
+    vals = synth.to_ratings(torch.from_numpy(pred))
+    tr = d.train
+    idx = np.ascontiguousarray(d.idx[:, tr].numpy())
+    x = vals[tr].double().numpy()
+    A, B = synth.initial_factors(w, mean_value=float(x.mean()))
+    return w, idx, x, [a.double().numpy() for a in A], [b.double().numpy() for b in B]
+
+
+def time_oracle_step(idx, x, A, B):
+    import oracle
+    t = time.perf_counter()
+    A = oracle.factor_epoch(A, B, idx, x, 1, LR, LAM)
+    B = oracle.core_epoch(A, B, idx, x, LR, LAM, nthreads=1)
+    return time.perf_counter() - t, A, B
+
+
+def cpu_baseline(nnz_sample):
+    w, idx, x, A, B = oracle_sample(nnz_sample)
+    dt, _, _ = time_oracle_step(idx, x, A, B)
+    n = int(x.shape[0])
+    return {"value": n / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{n} training nonzeros of the same recipe drawn at {nnz_sample} coordinates; "
+                      f"one sequential FP64 factor epoch (S=1) + core epoch, single thread, "
+                      f"{dt:.1f} s"}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return None
+    w, idx, x, A, B = oracle_sample(args.ref_sample)
+    n = int(x.shape[0])
+    for _ in range(args.warmup):
+        _, A, B = time_oracle_step(idx, x, A, B)
+    ts = []
+    for _ in range(args.steps):
+        dt, A, B = time_oracle_step(idx, x, A, B)
+        ts.append(dt)
+    tot = sum(ts)
+    value = n * len(ts) / tot
+    return {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / len(ts),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (seeded Zipf coordinates, planted-model ratings; Netflix-shaped)",
+        "config": {"workload": WORKLOAD, "N": w.N, "I": list(w.I), "J": list(w.J), "R": w.R,
+                   "nnz_train_sample": n, "precision": "fp64", "scatter": "sequential"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"{n} training nonzeros per step (same recipe at {args.ref_sample} "
+                                   f"coordinates), sequential FP64 factor + core epoch, 1 thread"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--precision", choices=["fp32", "tf32", "bf16"], default="fp32")
+    ap.add_argument("--cpu-sample", type=int, default=2_000_000)
+    ap.add_argument("--ref-sample", type=int, default=1_000_000)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(3, args.warmup)
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        backend = "nccl" if args.impl == "ours" else "gloo"
+        if backend == "nccl":
+            torch.cuda.set_device(local_rank)
+        torch.distributed.init_process_group(backend)
+    try:
+        if args.impl == "reference":
+            out = run_reference(args, rank, world)
+        else:
+            out = run_ours(args, rank, world, local_rank)
+        if out is not None:
+            print(json.dumps(out), flush=True)
+    finally:
+        if world > 1:
+            torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

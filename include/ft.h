@@ -1,0 +1,163 @@
+/*
+ * ft.h -- C ABI of the GB300 (sm_103a) FastTuckerPlus library.
+ *
+ * The library runs the stochastic epoch of sparse FastTucker decomposition
+ * as described in "cuFastTuckerPlus: A Stochastic Parallel Sparse FastTucker
+ * Decomposition Using GPU Tensor Cores" (arXiv 2404.10087):
+ *
+ *   model       xhat = sum_r prod_n c^(n)_r,  c^(n) = a^(n)_{i_n,:} B^(n)
+ *               (Sec. 2.3, Eq. "fasttucker"; Kruskal core of
+ *               Eq. "fasttucker_core_tensor")
+ *   factor phase  for every sampled nonzero, all N rows a^(n)_{i_n,:} move
+ *               together: a <- a + gamma_A((x - xhat) d^(n) B^(n)T - lambda_A a)
+ *               with d^(n) = prod_{k != n} c^(k)  (Sec. 3.1,
+ *               Eq. "Update_FastTuckerPlus_factor", Algorithm 3, Algorithm 4)
+ *   core phase  G^(n) = sum_Omega (xhat - x) a^(n)T d^(n);
+ *               B^(n) <- B^(n) - gamma_B (G^(n)/|Omega| + lambda_B B^(n))
+ *               (Eq. "Update_FastTuckerPlus_core", Algorithm 5)
+ *   errors      RMSE and MAE on a test set (Sec. 5.2)
+ *
+ * Conventions shared by every call:
+ *   - Pointers documented as "device" must point to memory of the current
+ *     CUDA device; "host" pointers to ordinary host memory.  Arrays of
+ *     pointers (idx, A, B, row_step_scale) are host arrays of N device
+ *     pointers.
+ *   - Coordinates are int32, 0-based, structure-of-arrays: idx[n][m] is the
+ *     mode-n index of nonzero m.  The stored order of the nonzeros is the
+ *     sampling order of the epoch (the caller shuffles them).
+ *   - A^(n) is float32 row-major I_n x J_n; B^(n) is float32 row-major
+ *     J_n x R.  Both are caller-owned, borrowed by the context, and updated
+ *     in place by the epochs.
+ *   - Supported shapes: 1 <= N <= 8, 1 <= J_n <= 32, 1 <= R <= 32, with
+ *     N * K <= 128 where K = 16 if max(J_n, R) <= 16, else 32.  Others
+ *     return FT_ERR_SHAPE.  nnz < 2^31.
+ *   - The library allocates no device memory: all scratch lives in a
+ *     caller-provided workspace (ft_workspace_size), 256-byte aligned.
+ *     The context itself is the only (host-heap) allocation.
+ *   - Calls are asynchronous on the given stream (a cudaStream_t passed as
+ *     void*; NULL = legacy default stream) unless stated otherwise.
+ *   - Errors are status codes; nothing is thrown across the ABI.  A
+ *     non-finite residual met inside a kernel is latched in the workspace
+ *     and reported by the next synchronising call (ft_rmse, ft_check) as
+ *     FT_ERR_NONFINITE.
+ */
+#ifndef FT_GB300_H
+#define FT_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define FT_MAX_ORDER 8
+#define FT_MAX_RANK 32
+
+typedef struct ft_ctx ft_ctx;
+
+typedef enum {
+  FT_OK = 0,
+  FT_ERR_ARG = -1,        /* null pointer, negative size, bad enum */
+  FT_ERR_INDEX = -2,      /* a coordinate outside [0, I_n) */
+  FT_ERR_SHAPE = -3,      /* N, J_n or R outside the supported set */
+  FT_ERR_CUDA = -4,       /* a CUDA runtime call failed */
+  FT_ERR_NONFINITE = -5,  /* a value or residual is NaN or infinite */
+  FT_ERR_TIMEOUT = -6,    /* a bounded device wait gave up */
+  FT_ERR_WORKSPACE = -7   /* workspace too small or misaligned */
+} ft_status;
+
+/* Arithmetic of the two contractions a.B and d.B^T (and of E^T D in the core
+ * phase).  Factor and core matrices always stay float32 masters; the
+ * accumulators are float32 in every mode (Sec. 4.1 uses FP16 inputs with
+ * tensor cores; this library offers plain FP32 on the CUDA cores, TF32 and
+ * BF16 on the tensor cores). */
+enum { FT_FP32 = 0, FT_TF32 = 1, FT_BF16 = 2 };
+
+/* How the factor phase writes rows back.
+ * FT_HOGWILD: every warp stores its updated rows directly, as the paper's
+ *   kernel does (Algorithm 4); concurrent updates of one row may be lost.
+ * FT_DETERMINISTIC: batch-synchronous epoch with batch size det_batch:
+ *   every nonzero of a batch reads the factors as they were at the batch
+ *   start, the per-nonzero steps of each row are summed in increasing
+ *   nonzero order and applied once; results are reproducible bit for bit. */
+enum { FT_HOGWILD = 0, FT_DETERMINISTIC = 1 };
+
+typedef struct {
+  int precision;       /* FT_FP32 | FT_TF32 | FT_BF16 */
+  int scatter;         /* FT_HOGWILD | FT_DETERMINISTIC */
+  int64_t det_batch;   /* batch size S of FT_DETERMINISTIC (>= 1) */
+  int blocks_per_sm;   /* persistent CTAs per SM; 0 = from the occupancy API */
+  int reserved[7];     /* must be zero */
+} ft_config;
+
+/* Fill *cfg with the defaults: FT_FP32, FT_HOGWILD, det_batch 4096, auto. */
+void ft_config_default(ft_config *cfg);
+
+/* Bytes of device workspace needed by ft_init for this problem (host call;
+ * queries the current device).  I, J: host arrays of N entries. */
+ft_status ft_workspace_size(int N, const int64_t *I, const int *J, int R, int64_t nnz,
+                            const ft_config *cfg, size_t *bytes);
+
+/* Create a context over the training nonzeros.
+ *   idx   host array of N device pointers, each nnz int32 coordinates
+ *   vals  device, nnz float32 values
+ *   A, B  host arrays of N device pointers (row-major float32, see above)
+ *   workspace  device, >= ft_workspace_size bytes, 256-byte aligned; owned by
+ *         the caller and used by every later call on this context
+ * Validates shapes, checks every coordinate and value on the device
+ * (FT_ERR_INDEX / FT_ERR_NONFINITE) and, in FT_DETERMINISTIC mode, builds the
+ * per-batch row grouping (a host sort over a copy of the coordinates).
+ * Synchronises the stream.  On success *out receives the context. */
+ft_status ft_init(ft_ctx **out, int N, const int64_t *I, const int *J, int R, int64_t nnz,
+                  const int32_t *const *idx, const float *vals, float *const *A,
+                  float *const *B, void *workspace, size_t ws_bytes, const ft_config *cfg,
+                  void *stream);
+
+/* One factor phase over all nnz training nonzeros in stored order
+ * (Algorithm 3 factor loop; Algorithm 4).  Step gamma_A = lr_a, lambda_A =
+ * lambda_a.  row_step_scale: NULL, or a host array of N pointers, each NULL
+ * or a device array of I_n per-row step multipliers s (the step of row i of
+ * mode n becomes lr_a * s[i]). */
+ft_status ft_epoch_factors(ft_ctx *ctx, float lr_a, float lambda_a,
+                           const float *const *row_step_scale, void *stream);
+
+/* One core phase (Algorithm 5): accumulate G^(n) over all training
+ * nonzeros with compensated float32 sums in a fixed order (reproducible bit
+ * for bit), then B^(n) <- B^(n) - lr_b (G^(n)/nnz + lambda_b B^(n)). */
+ft_status ft_epoch_core(ft_ctx *ctx, float lr_b, float lambda_b, void *stream);
+
+/* The core gradient alone, without touching B:
+ * G_out (device) receives G^(n) = sum_Omega (xhat - x) a^(n)T d^(n) for
+ * n = 0..N-1, each J_n x R row-major, concatenated. */
+ft_status ft_core_grad(ft_ctx *ctx, float *G_out, void *stream);
+
+/* Predictions xhat (float32) of n coordinates (idx: host array of N device
+ * pointers; out: device, n floats) with the context's current A and B. */
+ft_status ft_predict(ft_ctx *ctx, int64_t n, const int32_t *const *idx, float *out,
+                     void *stream);
+
+/* Errors on n coordinates with values vals (device): the residuals are
+ * float32, their sums are reduced in float64.  out3 (host) receives
+ * {RMSE, MAE, sum of squared errors}.  Synchronises the stream; returns
+ * FT_ERR_NONFINITE if an earlier kernel latched a non-finite residual. */
+ft_status ft_rmse(ft_ctx *ctx, int64_t n, const int32_t *const *idx, const float *vals,
+                  double *out3, void *stream);
+
+/* Synchronise the stream and report (then clear) the latched device error. */
+ft_status ft_check(ft_ctx *ctx, void *stream);
+
+/* Number of kernel launches issued by this context since ft_init. */
+int64_t ft_launch_count(const ft_ctx *ctx);
+
+/* Free the context (not the caller's buffers).  NULL is ignored. */
+void ft_destroy(ft_ctx *ctx);
+
+/* Static, human-readable name of a status. */
+const char *ft_status_str(ft_status s);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FT_GB300_H */

@@ -1,0 +1,600 @@
+// C ABI of the FastTuckerPlus library (declared in include/ft.h) and the small
+// kernels around the epochs: input validation, the deterministic per-row
+// reduction, the core finalize step and the float64 error reduction.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "ft.h"
+#include "ft_device.cuh"
+#include "ft_internal.h"
+
+namespace {
+
+constexpr size_t kAlign = 256;
+constexpr int kMaxCoreBlocksPerSm = 8;
+
+size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
+
+// ---------------------------------------------------------------- kernels
+struct ValidateArgs {
+  const int32_t *idx[FT_MAXN];
+  int64_t I[FT_MAXN];
+  int N;
+  const float *vals;
+  int64_t nnz;
+  int *err;
+};
+
+// Every coordinate in [0, I_n) and every value finite (ft_init).
+__global__ void k_validate(const ValidateArgs v) {
+  int bad = 0;
+  for (int64_t m = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; m < v.nnz;
+       m += int64_t(gridDim.x) * blockDim.x) {
+    for (int n = 0; n < v.N; ++n) {
+      const int32_t i = v.idx[n][m];
+      if (i < 0 || i >= v.I[n]) bad |= ft::ERRBIT_INDEX;
+    }
+    if (!isfinite(v.vals[m])) bad |= ft::ERRBIT_VALUE;
+  }
+  bad = __reduce_or_sync(ft::FULL, bad);
+  if (bad && (threadIdx.x & 31) == 0) atomicOr(v.err, bad);
+}
+
+struct ApplyArgs {
+  float *A[FT_MAXN];
+  const float *scale[FT_MAXN];
+  const int32_t *order[FT_MAXN];
+  const int32_t *segptr[FT_MAXN];
+  const int32_t *segrow[FT_MAXN];
+  int J[FT_MAXN];
+  int offJ[FT_MAXN];
+  int64_t seg_lo[FT_MAXN];
+  int64_t thread_off[FT_MAXN + 1];  // prefix sums of nseg_n * J_n
+  int N;
+  int sumJ;
+  const float *delta;
+  float lr;
+};
+
+// Deterministic scatter of one batch: for every (mode, row touched in the
+// batch, column) the per-nonzero steps are summed in increasing nonzero
+// order, then a <- a + lr * s_row * sum (batch-synchronous reading of
+// Eq. "Update_FastTuckerPlus_factor").
+__global__ void k_apply(const ApplyArgs a) {
+  const int64_t tid = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (tid >= a.thread_off[a.N]) return;
+  int n = 0;
+  while (tid >= a.thread_off[n + 1]) ++n;
+  const int64_t local = tid - a.thread_off[n];
+  const int64_t seg = a.seg_lo[n] + local / a.J[n];
+  const int j = int(local % a.J[n]);
+  const int32_t p0 = a.segptr[n][seg], p1 = a.segptr[n][seg + 1];
+  float acc = 0.f;
+  for (int32_t q = p0; q < p1; ++q) acc += a.delta[int64_t(a.order[n][q]) * a.sumJ + a.offJ[n] + j];
+  const int64_t row = a.segrow[n][seg];
+  const float lr = a.scale[n] ? a.lr * a.scale[n][row] : a.lr;
+  float *dst = a.A[n] + row * a.J[n] + j;
+  *dst = fmaf(lr, acc, *dst);
+}
+
+struct FinalizeArgs {
+  const float *partial;  // [nparts][N][K][K] of (sum, comp)
+  int nparts;
+  int N, K, R;
+  int J[FT_MAXN];
+  int offG[FT_MAXN];
+  float *B[FT_MAXN];
+  float *G_out;
+  float lr, lam;
+  float inv_nnz;
+  int update;
+};
+
+// Core finalize (Algorithm 5): G^(n) = sum over CTA partials (compensated,
+// fixed order); B <- B - lr (G / |Omega| + lam B).
+__global__ void k_finalize(const FinalizeArgs f) {
+  const int tid = blockIdx.x * blockDim.x + threadIdx.x;
+  const int KK = f.K * f.K;
+  if (tid >= f.N * KK) return;
+  const int n = tid / KK, j = (tid % KK) / f.K, r = tid % f.K;
+  if (j >= f.J[n] || r >= f.R) return;
+  float s = 0.f, c = 0.f;
+  for (int q = 0; q < f.nparts; ++q) {
+    const float *pp = f.partial + (size_t(q) * f.N * KK + tid) * 2;
+    ft::neumaier_add(s, c, pp[0]);
+    c += pp[1];
+  }
+  const float G = s + c;
+  if (f.G_out) f.G_out[f.offG[n] + j * f.R + r] = G;
+  if (f.update) {
+    float *b = f.B[n] + j * f.R + r;
+    const float bv = *b;
+    *b = bv - f.lr * fmaf(G, f.inv_nnz, f.lam * bv);
+  }
+}
+
+struct ErrFinalArgs {
+  const double *part;
+  int nparts;
+  int64_t n;
+  double *out3;
+};
+
+// Fixed-order float64 reduction of the per-CTA error sums.
+__global__ void k_errors_final(const ErrFinalArgs a) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  double se = 0.0, ae = 0.0;
+  for (int q = 0; q < a.nparts; ++q) { se += a.part[2 * q]; ae += a.part[2 * q + 1]; }
+  a.out3[0] = a.n > 0 ? sqrt(se / double(a.n)) : 0.0;
+  a.out3[1] = a.n > 0 ? ae / double(a.n) : 0.0;
+  a.out3[2] = se;
+}
+
+// ------------------------------------------------------------------- plan
+struct Plan {
+  int N = 0, R = 0, K = 0, sumJ = 0;
+  int J[FT_MAXN] = {0};
+  int offJ[FT_MAXN] = {0};
+  int64_t I[FT_MAXN] = {0};
+  int64_t nnz = 0;
+  ft_config cfg{};
+  int dev = 0, num_sms = 0;
+  ft::KernelSet ks;
+  ft::EvalSet es;
+  int grid_factor = 0, grid_core = 0, grid_eval = 0;
+  int64_t det_S = 0, nbatches = 0;
+  // workspace offsets
+  size_t off_err = 0, off_out = 0, off_partial = 0, off_errpart = 0, off_delta = 0;
+  size_t off_order = 0, off_segptr = 0, off_segrow = 0, total = 0;
+};
+
+ft_status cuda_status(cudaError_t e) { return e == cudaSuccess ? FT_OK : FT_ERR_CUDA; }
+
+int occupancy(const void *fn, int threads, size_t smem) {
+  int nb = 0;
+  if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)) != cudaSuccess)
+    return 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, threads, smem) != cudaSuccess) return 0;
+  return nb;
+}
+
+ft_status make_plan(int N, const int64_t *I, const int *J, int R, int64_t nnz, const ft_config *cfg,
+                    Plan *p) {
+  if (!I || !J || !p) return FT_ERR_ARG;
+  if (N < 1 || N > FT_MAX_ORDER) return FT_ERR_SHAPE;
+  if (R < 1 || R > FT_MAX_RANK) return FT_ERR_SHAPE;
+  if (nnz < 0 || nnz > INT32_MAX) return FT_ERR_ARG;
+  ft_config c;
+  ft_config_default(&c);
+  if (cfg) c = *cfg;
+  if (c.precision < FT_FP32 || c.precision > FT_BF16) return FT_ERR_ARG;
+  if (c.scatter != FT_HOGWILD && c.scatter != FT_DETERMINISTIC) return FT_ERR_ARG;
+  if (c.scatter == FT_DETERMINISTIC && c.det_batch < 1) return FT_ERR_ARG;
+  if (c.blocks_per_sm < 0) return FT_ERR_ARG;
+  int maxr = R;
+  p->sumJ = 0;
+  for (int n = 0; n < N; ++n) {
+    if (J[n] < 1 || J[n] > FT_MAX_RANK) return FT_ERR_SHAPE;
+    if (I[n] < 1 || I[n] > INT32_MAX) return FT_ERR_SHAPE;
+    maxr = std::max(maxr, J[n]);
+    p->J[n] = J[n];
+    p->I[n] = I[n];
+    p->offJ[n] = p->sumJ;
+    p->sumJ += J[n];
+  }
+  const int K = maxr <= 16 ? 16 : 32;
+  if (N * K > 128) return FT_ERR_SHAPE;
+  p->N = N;
+  p->R = R;
+  p->K = K;
+  p->nnz = nnz;
+  p->cfg = c;
+  bool ok = false;
+  switch (K * 10 + c.precision) {
+    case 160: ok = ft_kernels_16_0(N, &p->ks); break;
+    case 161: ok = ft_kernels_16_1(N, &p->ks); break;
+    case 162: ok = ft_kernels_16_2(N, &p->ks); break;
+    case 320: ok = ft_kernels_32_0(N, &p->ks); break;
+    case 321: ok = ft_kernels_32_1(N, &p->ks); break;
+    case 322: ok = ft_kernels_32_2(N, &p->ks); break;
+  }
+  if (!ok) return FT_ERR_SHAPE;
+  ok = K == 16 ? ft_eval_16(N, &p->es) : ft_eval_32(N, &p->es);
+  if (!ok) return FT_ERR_SHAPE;
+
+  if (cudaGetDevice(&p->dev) != cudaSuccess) return FT_ERR_CUDA;
+  if (cudaDeviceGetAttribute(&p->num_sms, cudaDevAttrMultiProcessorCount, p->dev) != cudaSuccess)
+    return FT_ERR_CUDA;
+  const int occ_f = occupancy(p->ks.factor, 256, p->ks.factor_smem);
+  const int occ_d = occupancy(p->ks.factor_delta, 256, p->ks.factor_smem);
+  const int occ_c = occupancy(p->ks.core, p->ks.core_threads, p->ks.core_smem);
+  const int occ_p = occupancy(p->es.predict, 256, p->es.smem);
+  const int occ_e = occupancy(p->es.errors, 256, p->es.smem);
+  if (occ_f < 1 || occ_d < 1 || occ_c < 1 || occ_p < 1 || occ_e < 1) return FT_ERR_CUDA;
+  const int bps = c.blocks_per_sm;
+  p->grid_factor = p->num_sms * (bps ? bps : std::min(occ_f, occ_d));
+  p->grid_core = p->num_sms * std::min(bps ? bps : occ_c, kMaxCoreBlocksPerSm);
+  p->grid_eval = p->num_sms * std::min(occ_p, occ_e);
+
+  size_t off = 0;
+  p->off_err = off;     off += align_up(sizeof(int) * 16);
+  p->off_out = off;     off += align_up(sizeof(double) * 4);
+  p->off_partial = off; off += align_up(sizeof(float) * 2 * size_t(p->grid_core) * N * K * K);
+  p->off_errpart = off; off += align_up(sizeof(double) * 2 * size_t(p->grid_eval));
+  if (c.scatter == FT_DETERMINISTIC) {
+    p->det_S = std::max<int64_t>(1, std::min<int64_t>(c.det_batch, std::max<int64_t>(nnz, 1)));
+    p->nbatches = nnz > 0 ? (nnz + p->det_S - 1) / p->det_S : 0;
+    p->off_delta = off;  off += align_up(sizeof(float) * size_t(p->det_S) * p->sumJ);
+    p->off_order = off;  off += align_up(sizeof(int32_t) * size_t(N) * nnz);
+    p->off_segptr = off; off += align_up(sizeof(int32_t) * size_t(N) * (nnz + 1));
+    p->off_segrow = off; off += align_up(sizeof(int32_t) * size_t(N) * std::max<int64_t>(nnz, 1));
+  }
+  p->total = off;
+  return FT_OK;
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ context
+struct ft_ctx {
+  Plan p;
+  const int32_t *idx[FT_MAXN] = {nullptr};
+  const float *vals = nullptr;
+  float *A[FT_MAXN] = {nullptr};
+  float *B[FT_MAXN] = {nullptr};
+  char *ws = nullptr;
+  unsigned vecmask = 0;
+  std::vector<int64_t> seg_lo[FT_MAXN];  // per mode: first segment of each batch (+ end)
+  int64_t launches = 0;
+};
+
+namespace {
+
+template <typename T>
+T *ws_ptr(ft_ctx *c, size_t off) {
+  return reinterpret_cast<T *>(c->ws + off);
+}
+
+ft_status launch(ft_ctx *c, const void *fn, int grid, int threads, size_t smem, void *args,
+                 cudaStream_t st) {
+  if (grid <= 0) return FT_OK;
+  void *argv[] = {args};
+  const cudaError_t e = cudaLaunchKernel(fn, dim3(grid), dim3(threads), argv, smem, st);
+  ++c->launches;
+  return cuda_status(e);
+}
+
+ft::EpochArgs base_args(ft_ctx *c) {
+  ft::EpochArgs a;
+  memset(&a, 0, sizeof(a));
+  for (int n = 0; n < c->p.N; ++n) {
+    a.idx[n] = c->idx[n];
+    a.A[n] = c->A[n];
+    a.B[n] = c->B[n];
+    a.I[n] = c->p.I[n];
+    a.J[n] = c->p.J[n];
+    a.offJ[n] = c->p.offJ[n];
+  }
+  a.R = c->p.R;
+  a.sumJ = c->p.sumJ;
+  a.vecmask = c->vecmask;
+  a.vals = c->vals;
+  a.begin = 0;
+  a.end = c->p.nnz;
+  a.err = ws_ptr<int>(c, c->p.off_err);
+  return a;
+}
+
+// Host construction of the deterministic row grouping: for every batch and
+// mode, the batch's positions sorted by (row, position) and cut into one
+// segment per distinct row.
+ft_status build_segments(ft_ctx *c, cudaStream_t st) {
+  const Plan &p = c->p;
+  const int64_t nnz = p.nnz, S = p.det_S;
+  std::vector<int32_t> host_idx(size_t(std::max<int64_t>(nnz, 1)));
+  std::vector<int32_t> order(size_t(std::max<int64_t>(nnz, 1)));
+  std::vector<int32_t> segptr, segrow;
+  std::vector<uint64_t> keys(size_t(std::min<int64_t>(S, std::max<int64_t>(nnz, 1))));
+  for (int n = 0; n < p.N; ++n) {
+    if (nnz > 0 && cudaMemcpyAsync(host_idx.data(), c->idx[n], sizeof(int32_t) * nnz,
+                                   cudaMemcpyDeviceToHost, st) != cudaSuccess)
+      return FT_ERR_CUDA;
+    if (cudaStreamSynchronize(st) != cudaSuccess) return FT_ERR_CUDA;
+    segptr.clear();
+    segrow.clear();
+    c->seg_lo[n].assign(size_t(p.nbatches + 1), 0);
+    for (int64_t b = 0; b < p.nbatches; ++b) {
+      const int64_t lo = b * S, hi = std::min(nnz, lo + S);
+      c->seg_lo[n][b] = int64_t(segrow.size());
+      for (int64_t m = lo; m < hi; ++m)
+        keys[size_t(m - lo)] = (uint64_t(uint32_t(host_idx[m])) << 32) | uint64_t(m - lo);
+      std::sort(keys.begin(), keys.begin() + (hi - lo));
+      int64_t prev = -1;
+      for (int64_t k = 0; k < hi - lo; ++k) {
+        const int64_t row = int64_t(keys[k] >> 32);
+        order[size_t(lo + k)] = int32_t(keys[k] & 0xffffffffu);
+        if (row != prev) {
+          segptr.push_back(int32_t(lo + k));
+          segrow.push_back(int32_t(row));
+          prev = row;
+        }
+      }
+    }
+    c->seg_lo[n][p.nbatches] = int64_t(segrow.size());
+    segptr.push_back(int32_t(nnz));
+    int32_t *d_order = ws_ptr<int32_t>(c, p.off_order) + size_t(n) * nnz;
+    int32_t *d_segptr = ws_ptr<int32_t>(c, p.off_segptr) + size_t(n) * (nnz + 1);
+    int32_t *d_segrow = ws_ptr<int32_t>(c, p.off_segrow) + size_t(n) * std::max<int64_t>(nnz, 1);
+    if (nnz > 0 && cudaMemcpyAsync(d_order, order.data(), sizeof(int32_t) * nnz, cudaMemcpyHostToDevice, st) !=
+                       cudaSuccess)
+      return FT_ERR_CUDA;
+    if (cudaMemcpyAsync(d_segptr, segptr.data(), sizeof(int32_t) * segptr.size(), cudaMemcpyHostToDevice, st) !=
+        cudaSuccess)
+      return FT_ERR_CUDA;
+    if (!segrow.empty() && cudaMemcpyAsync(d_segrow, segrow.data(), sizeof(int32_t) * segrow.size(),
+                                           cudaMemcpyHostToDevice, st) != cudaSuccess)
+      return FT_ERR_CUDA;
+    if (cudaStreamSynchronize(st) != cudaSuccess) return FT_ERR_CUDA;
+  }
+  return FT_OK;
+}
+
+ft_status take_error(ft_ctx *c, cudaStream_t st) {
+  int err = 0;
+  int *d = ws_ptr<int>(c, c->p.off_err);
+  if (cudaMemcpyAsync(&err, d, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess) return FT_ERR_CUDA;
+  if (cudaStreamSynchronize(st) != cudaSuccess) return FT_ERR_CUDA;
+  if (err == 0) return FT_OK;
+  if (cudaMemsetAsync(d, 0, sizeof(int), st) != cudaSuccess) return FT_ERR_CUDA;
+  if (err & ft::ERRBIT_INDEX) return FT_ERR_INDEX;
+  return FT_ERR_NONFINITE;
+}
+
+}  // namespace
+
+// ======================================================================= ABI
+extern "C" {
+
+void ft_config_default(ft_config *cfg) {
+  if (!cfg) return;
+  memset(cfg, 0, sizeof(*cfg));
+  cfg->precision = FT_FP32;
+  cfg->scatter = FT_HOGWILD;
+  cfg->det_batch = 4096;
+  cfg->blocks_per_sm = 0;
+}
+
+ft_status ft_workspace_size(int N, const int64_t *I, const int *J, int R, int64_t nnz,
+                            const ft_config *cfg, size_t *bytes) {
+  if (!bytes) return FT_ERR_ARG;
+  Plan p;
+  const ft_status s = make_plan(N, I, J, R, nnz, cfg, &p);
+  if (s != FT_OK) return s;
+  *bytes = p.total;
+  return FT_OK;
+}
+
+ft_status ft_init(ft_ctx **out, int N, const int64_t *I, const int *J, int R, int64_t nnz,
+                  const int32_t *const *idx, const float *vals, float *const *A, float *const *B,
+                  void *workspace, size_t ws_bytes, const ft_config *cfg, void *stream) {
+  if (!out || !idx || !A || !B || (nnz > 0 && !vals) || !workspace) return FT_ERR_ARG;
+  *out = nullptr;
+  ft_ctx *c = new (std::nothrow) ft_ctx();
+  if (!c) return FT_ERR_ARG;
+  ft_status s = make_plan(N, I, J, R, nnz, cfg, &c->p);
+  if (s != FT_OK) { delete c; return s; }
+  if (ws_bytes < c->p.total || (reinterpret_cast<uintptr_t>(workspace) % kAlign) != 0) {
+    delete c;
+    return FT_ERR_WORKSPACE;
+  }
+  for (int n = 0; n < N; ++n) {
+    if ((nnz > 0 && !idx[n]) || !A[n] || !B[n]) { delete c; return FT_ERR_ARG; }
+    c->idx[n] = idx[n];
+    c->A[n] = A[n];
+    c->B[n] = B[n];
+    // full 16-byte row chunks: rows exactly K wide and a 16-byte aligned base
+    if (J[n] == c->p.K && (reinterpret_cast<uintptr_t>(A[n]) % 16) == 0) c->vecmask |= 1u << n;
+  }
+  c->vals = vals;
+  c->ws = static_cast<char *>(workspace);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (cudaMemsetAsync(c->ws, 0, c->p.off_partial, st) != cudaSuccess) { delete c; return FT_ERR_CUDA; }
+  if (nnz > 0) {
+    ValidateArgs v;
+    memset(&v, 0, sizeof(v));
+    for (int n = 0; n < N; ++n) { v.idx[n] = idx[n]; v.I[n] = I[n]; }
+    v.N = N;
+    v.vals = vals;
+    v.nnz = nnz;
+    v.err = ws_ptr<int>(c, c->p.off_err);
+    const int grid = int(std::min<int64_t>((nnz + 255) / 256, int64_t(c->p.num_sms) * 8));
+    s = launch(c, reinterpret_cast<const void *>(&k_validate), grid, 256, 0, &v, st);
+    if (s != FT_OK) { delete c; return s; }
+    int err = 0;
+    if (cudaMemcpyAsync(&err, v.err, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess) {
+      delete c;
+      return FT_ERR_CUDA;
+    }
+    if (err & ft::ERRBIT_INDEX) { delete c; return FT_ERR_INDEX; }
+    if (err & ft::ERRBIT_VALUE) { delete c; return FT_ERR_NONFINITE; }
+  }
+  if (c->p.cfg.scatter == FT_DETERMINISTIC) {
+    s = build_segments(c, st);
+    if (s != FT_OK) { delete c; return s; }
+  }
+  if (cudaStreamSynchronize(st) != cudaSuccess) { delete c; return FT_ERR_CUDA; }
+  *out = c;
+  return FT_OK;
+}
+
+ft_status ft_epoch_factors(ft_ctx *c, float lr_a, float lambda_a, const float *const *row_step_scale,
+                           void *stream) {
+  if (!c) return FT_ERR_ARG;
+  if (!std::isfinite(lr_a) || !std::isfinite(lambda_a)) return FT_ERR_ARG;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const Plan &p = c->p;
+  if (p.nnz == 0) return FT_OK;
+  ft::EpochArgs a = base_args(c);
+  a.lr = lr_a;
+  a.lam = lambda_a;
+  if (row_step_scale)
+    for (int n = 0; n < p.N; ++n) a.scale[n] = row_step_scale[n];
+  if (p.cfg.scatter == FT_HOGWILD)
+    return launch(c, p.ks.factor, p.grid_factor, 256, p.ks.factor_smem, &a, st);
+
+  a.delta = ws_ptr<float>(c, p.off_delta);
+  ApplyArgs ap;
+  memset(&ap, 0, sizeof(ap));
+  ap.N = p.N;
+  ap.sumJ = p.sumJ;
+  ap.delta = a.delta;
+  ap.lr = lr_a;
+  for (int n = 0; n < p.N; ++n) {
+    ap.A[n] = c->A[n];
+    ap.scale[n] = a.scale[n];
+    ap.order[n] = ws_ptr<int32_t>(c, p.off_order) + size_t(n) * p.nnz;
+    ap.segptr[n] = ws_ptr<int32_t>(c, p.off_segptr) + size_t(n) * (p.nnz + 1);
+    ap.segrow[n] = ws_ptr<int32_t>(c, p.off_segrow) + size_t(n) * std::max<int64_t>(p.nnz, 1);
+    ap.J[n] = p.J[n];
+    ap.offJ[n] = p.offJ[n];
+  }
+  for (int64_t b = 0; b < p.nbatches; ++b) {
+    a.begin = b * p.det_S;
+    a.end = std::min(p.nnz, a.begin + p.det_S);
+    const int64_t tiles = (a.end - a.begin + FT_TILE - 1) / FT_TILE;
+    const int grid = int(std::min<int64_t>(p.grid_factor, (tiles + 7) / 8));
+    ft_status s = launch(c, p.ks.factor_delta, grid, 256, p.ks.factor_smem, &a, st);
+    if (s != FT_OK) return s;
+    ap.thread_off[0] = 0;
+    for (int n = 0; n < p.N; ++n) {
+      ap.seg_lo[n] = c->seg_lo[n][b];
+      const int64_t nseg = c->seg_lo[n][b + 1] - c->seg_lo[n][b];
+      ap.thread_off[n + 1] = ap.thread_off[n] + nseg * p.J[n];
+    }
+    const int64_t nthr = ap.thread_off[p.N];
+    s = launch(c, reinterpret_cast<const void *>(&k_apply), int((nthr + 255) / 256), 256, 0, &ap, st);
+    if (s != FT_OK) return s;
+  }
+  return FT_OK;
+}
+
+static ft_status core_pass(ft_ctx *c, float lr_b, float lambda_b, float *G_out, int update,
+                           cudaStream_t st) {
+  const Plan &p = c->p;
+  ft::EpochArgs a = base_args(c);
+  a.partial = ws_ptr<float>(c, p.off_partial);
+  ft_status s = launch(c, p.ks.core, p.grid_core, p.ks.core_threads, p.ks.core_smem, &a, st);
+  if (s != FT_OK) return s;
+  FinalizeArgs f;
+  memset(&f, 0, sizeof(f));
+  f.partial = a.partial;
+  f.nparts = p.grid_core;
+  f.N = p.N;
+  f.K = p.K;
+  f.R = p.R;
+  int off = 0;
+  for (int n = 0; n < p.N; ++n) {
+    f.J[n] = p.J[n];
+    f.B[n] = c->B[n];
+    f.offG[n] = off;
+    off += p.J[n] * p.R;
+  }
+  f.G_out = G_out;
+  f.lr = lr_b;
+  f.lam = lambda_b;
+  f.inv_nnz = p.nnz > 0 ? float(1.0 / double(p.nnz)) : 0.f;
+  f.update = update;
+  const int total = p.N * p.K * p.K;
+  return launch(c, reinterpret_cast<const void *>(&k_finalize), (total + 255) / 256, 256, 0, &f, st);
+}
+
+ft_status ft_epoch_core(ft_ctx *c, float lr_b, float lambda_b, void *stream) {
+  if (!c) return FT_ERR_ARG;
+  if (!std::isfinite(lr_b) || !std::isfinite(lambda_b)) return FT_ERR_ARG;
+  return core_pass(c, lr_b, lambda_b, nullptr, 1, static_cast<cudaStream_t>(stream));
+}
+
+ft_status ft_core_grad(ft_ctx *c, float *G_out, void *stream) {
+  if (!c || !G_out) return FT_ERR_ARG;
+  return core_pass(c, 0.f, 0.f, G_out, 0, static_cast<cudaStream_t>(stream));
+}
+
+static ft_status eval_args(ft_ctx *c, int64_t n, const int32_t *const *idx, ft::EpochArgs *a) {
+  if (n < 0 || n > INT32_MAX) return FT_ERR_ARG;
+  if (n > 0 && !idx) return FT_ERR_ARG;
+  *a = base_args(c);
+  for (int k = 0; k < c->p.N; ++k) {
+    if (n > 0 && !idx[k]) return FT_ERR_ARG;
+    a->idx[k] = n > 0 ? idx[k] : nullptr;
+  }
+  a->begin = 0;
+  a->end = n;
+  return FT_OK;
+}
+
+ft_status ft_predict(ft_ctx *c, int64_t n, const int32_t *const *idx, float *out, void *stream) {
+  if (!c || (n > 0 && !out)) return FT_ERR_ARG;
+  ft::EpochArgs a;
+  ft_status s = eval_args(c, n, idx, &a);
+  if (s != FT_OK || n == 0) return s;
+  a.pred = out;
+  const int64_t tiles = (n + FT_TILE - 1) / FT_TILE;
+  const int grid = int(std::min<int64_t>(c->p.grid_eval, (tiles + 7) / 8));
+  return launch(c, c->p.es.predict, grid, 256, c->p.es.smem, &a, static_cast<cudaStream_t>(stream));
+}
+
+ft_status ft_rmse(ft_ctx *c, int64_t n, const int32_t *const *idx, const float *vals, double *out3,
+                  void *stream) {
+  if (!c || !out3 || (n > 0 && !vals)) return FT_ERR_ARG;
+  ft::EpochArgs a;
+  ft_status s = eval_args(c, n, idx, &a);
+  if (s != FT_OK) return s;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  a.vals = vals;
+  a.err_partial = ws_ptr<double>(c, c->p.off_errpart);
+  const int grid = c->p.grid_eval;
+  s = launch(c, c->p.es.errors, grid, 256, c->p.es.smem, &a, st);
+  if (s != FT_OK) return s;
+  ErrFinalArgs fa;
+  fa.part = a.err_partial;
+  fa.nparts = grid;
+  fa.n = n;
+  fa.out3 = ws_ptr<double>(c, c->p.off_out);
+  s = launch(c, reinterpret_cast<const void *>(&k_errors_final), 1, 32, 0, &fa, st);
+  if (s != FT_OK) return s;
+  if (cudaMemcpyAsync(out3, fa.out3, sizeof(double) * 3, cudaMemcpyDeviceToHost, st) != cudaSuccess)
+    return FT_ERR_CUDA;
+  return take_error(c, st);
+}
+
+ft_status ft_check(ft_ctx *c, void *stream) {
+  if (!c) return FT_ERR_ARG;
+  return take_error(c, static_cast<cudaStream_t>(stream));
+}
+
+int64_t ft_launch_count(const ft_ctx *c) { return c ? c->launches : 0; }
+
+void ft_destroy(ft_ctx *c) { delete c; }
+
+const char *ft_status_str(ft_status s) {
+  switch (s) {
+    case FT_OK: return "ok";
+    case FT_ERR_ARG: return "invalid argument";
+    case FT_ERR_INDEX: return "coordinate out of range";
+    case FT_ERR_SHAPE: return "unsupported shape";
+    case FT_ERR_CUDA: return "CUDA error";
+    case FT_ERR_NONFINITE: return "non-finite value or residual";
+    case FT_ERR_TIMEOUT: return "device wait timed out";
+    case FT_ERR_WORKSPACE: return "workspace too small or misaligned";
+  }
+  return "unknown status";
+}
+
+}  // extern "C"

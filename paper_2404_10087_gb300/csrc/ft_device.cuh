@@ -1,0 +1,639 @@
+// Device side of the FastTuckerPlus epoch for sm_103a.
+//
+// Work decomposition (Sec. 4.3-4.4 of the paper: one warp per sample set Psi
+// of M = 16 nonzeros, grid-stride over the Psi): a warp owns a tile of 16
+// consecutive nonzeros.  Lane l = 4g + t (g = l / 4 in 0..7, t = l % 4 in
+// 0..3) holds tile rows g and g + 8, and in each of them the column chunk
+// [CPL*t, CPL*t + CPL) with CPL = K / 4, K the padded rank (16 or 32).
+// This "row-chunk" layout is shared by A_Psi (columns j), C_Psi and D_Psi
+// (columns r) and P = D B^T (columns j):
+//   * a chunk of a factor row is one 16-byte vector load per 4 columns;
+//   * the tensor-core products are arranged (by permuting the contraction
+//     index and the output columns, which the products allow) so that the
+//     mma.sync operand and accumulator fragments ARE the row-chunk layout -
+//     no shuffles or shared-memory round trips between C, D and P;
+//   * the Hadamard products for D (Algorithm 4) and the update are purely
+//     per-lane; the prediction and the residual take two xor-shuffles.
+// Zero padding of J_n, R up to K follows Sec. 4.2.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#define FT_MAXN 8
+#define FT_TILE 16
+
+namespace ft {
+
+enum Math { MATH_FP32 = 0, MATH_TF32 = 1, MATH_BF16 = 2 };
+
+// Latched device error bits (workspace word 0).
+enum : int { ERRBIT_NONFINITE = 1, ERRBIT_INDEX = 2, ERRBIT_VALUE = 4 };
+
+constexpr unsigned FULL = 0xffffffffu;
+
+// ---------------------------------------------------------------- arguments
+struct EpochArgs {
+  const int32_t *idx[FT_MAXN];      // coordinates of the processed nonzeros
+  float *A[FT_MAXN];                // factor matrices, row-major I_n x J_n
+  const float *B[FT_MAXN];          // core matrices, row-major J_n x R
+  const float *scale[FT_MAXN];      // per-row step multipliers or null
+  int64_t I[FT_MAXN];               // mode sizes (coordinates are bounds-checked)
+  int J[FT_MAXN];
+  int offJ[FT_MAXN];                // prefix sums of J_n (delta row layout)
+  int R;
+  int sumJ;
+  unsigned vecmask;                 // bit n: rows of mode n can be read as full 16-byte chunks
+  const float *vals;                // values
+  int64_t begin, end;               // processed nonzero range [begin, end)
+  float lr, lam;
+  float *delta;                     // deterministic mode: -grad rows, row m - begin
+  float *partial;                   // core phase: per-CTA (sum, comp) of G
+  float *pred;                      // predict: outputs (index m - begin)
+  double *err_partial;              // errors: per-CTA (sum e^2, sum |e|)
+  int *err;                         // latched error word
+};
+
+// ------------------------------------------------------------- small helpers
+__device__ __forceinline__ uint32_t to_tf32(float f) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(f));
+  return r;
+}
+
+__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
+  __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+  return *reinterpret_cast<uint32_t *>(&v);
+}
+
+__device__ __forceinline__ void mma_tf32(float (&d)[4], uint32_t a0, uint32_t a1, uint32_t a2,
+                                         uint32_t a3, uint32_t b0, uint32_t b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
+      "{%8,%9}, {%0,%1,%2,%3};\n"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+}
+
+__device__ __forceinline__ void mma_bf16(float (&d)[4], uint32_t a0, uint32_t a1, uint32_t a2,
+                                         uint32_t a3, uint32_t b0, uint32_t b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
+      "{%8,%9}, {%0,%1,%2,%3};\n"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+}
+
+// Output-column permutation of an n-tile: logical column 8u + c of the
+// accumulator is physical column pi(8u + c) = CPL*(c/2) + 2u + (c%2), so that
+// accumulator elements (c = 2t, 2t+1) land in the lane's own chunk.
+template <int K>
+__device__ __forceinline__ int out_col(int u, int c) {
+  return (K / 4) * (c >> 1) + 2 * u + (c & 1);
+}
+
+// M(k, col) of the two products a.B (which = 0: M = B, k = j, col = r) and
+// d.B^T (which = 1: M = B^T, k = r, col = j), zero outside J_n x R.
+__device__ __forceinline__ float core_entry(const float *__restrict__ Bn, int J, int R, int which,
+                                            int k, int col) {
+  if (which == 0) return (k < J && col < R) ? Bn[k * R + col] : 0.f;
+  return (col < J && k < R) ? Bn[col * R + k] : 0.f;
+}
+
+// ----------------------------------------------- y = x . M on a warp tile
+// x, y: [16 x K] in the row-chunk layout.  One table per (mode, product) in
+// shared memory, filled once per CTA.
+template <int K, int MATH>
+struct Prod;
+
+// Plain FP32 on the CUDA cores: the lane gathers the full rows of x by
+// shuffles within its group of four and multiplies by its column chunk of M.
+template <int K>
+struct Prod<K, MATH_FP32> {
+  static constexpr int CPL = K / 4;
+  static constexpr int WORDS = K * K;  // floats per table
+  __device__ static void fill(float *tab, const float *__restrict__ Bn, int J, int R, int which) {
+    for (int e = threadIdx.x; e < K * K; e += blockDim.x) tab[e] = core_entry(Bn, J, R, which, e / K, e % K);
+  }
+  __device__ static void run(const float (&x)[2][CPL], const float *tab, float (&y)[2][CPL], int lane) {
+    const int t = lane & 3;
+    const int base = lane & ~3;
+#pragma unroll
+    for (int q = 0; q < CPL; ++q) y[0][q] = y[1][q] = 0.f;
+#pragma unroll
+    for (int tt = 0; tt < 4; ++tt) {
+#pragma unroll
+      for (int qq = 0; qq < CPL; ++qq) {
+        const float v0 = __shfl_sync(FULL, x[0][qq], base | tt);
+        const float v1 = __shfl_sync(FULL, x[1][qq], base | tt);
+        const float *row = tab + (CPL * tt + qq) * K + CPL * t;
+        float m[CPL];
+        if constexpr (CPL % 4 == 0) {
+#pragma unroll
+          for (int w = 0; w < CPL; w += 4) {
+            const float4 f = *reinterpret_cast<const float4 *>(row + w);
+            m[w] = f.x; m[w + 1] = f.y; m[w + 2] = f.z; m[w + 3] = f.w;
+          }
+        } else {
+#pragma unroll
+          for (int w = 0; w < CPL; ++w) m[w] = row[w];
+        }
+#pragma unroll
+        for (int q = 0; q < CPL; ++q) {
+          y[0][q] = fmaf(v0, m[q], y[0][q]);
+          y[1][q] = fmaf(v1, m[q], y[1][q]);
+        }
+      }
+    }
+  }
+};
+
+// TF32 tensor cores, mma.sync m16n8k8.  k-step s, lane (g, t): logical k = t
+// is physical column CPL*t + 2s, logical k = t + 4 is CPL*t + 2s + 1.
+template <int K>
+struct Prod<K, MATH_TF32> {
+  static constexpr int CPL = K / 4;
+  static constexpr int NT = K / 8;   // n-tiles
+  static constexpr int KS = K / 8;   // k-steps
+  static constexpr int WORDS = NT * KS * 32 * 2;
+  __device__ static void fill(float *tabf, const float *__restrict__ Bn, int J, int R, int which) {
+    uint32_t *tab = reinterpret_cast<uint32_t *>(tabf);
+    for (int e = threadIdx.x; e < NT * KS * 32; e += blockDim.x) {
+      const int lane = e & 31, us = e >> 5, s = us % KS, u = us / KS;
+      const int g = lane >> 2, t = lane & 3;
+      const int col = out_col<K>(u, g);
+      const int k0 = CPL * t + 2 * s;
+      tab[2 * e] = to_tf32(core_entry(Bn, J, R, which, k0, col));
+      tab[2 * e + 1] = to_tf32(core_entry(Bn, J, R, which, k0 + 1, col));
+    }
+  }
+  __device__ static void run(const float (&x)[2][CPL], const float *tabf, float (&y)[2][CPL], int lane) {
+    const uint2 *tab = reinterpret_cast<const uint2 *>(tabf);
+    uint32_t xa[2][CPL];
+#pragma unroll
+    for (int q = 0; q < CPL; ++q) { xa[0][q] = to_tf32(x[0][q]); xa[1][q] = to_tf32(x[1][q]); }
+#pragma unroll
+    for (int u = 0; u < NT; ++u) {
+      float acc[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+      for (int s = 0; s < KS; ++s) {
+        const uint2 b = tab[(u * KS + s) * 32 + lane];
+        mma_tf32(acc, xa[0][2 * s], xa[1][2 * s], xa[0][2 * s + 1], xa[1][2 * s + 1], b.x, b.y);
+      }
+      y[0][2 * u] = acc[0]; y[0][2 * u + 1] = acc[1];
+      y[1][2 * u] = acc[2]; y[1][2 * u + 1] = acc[3];
+    }
+  }
+};
+
+// BF16 tensor cores, mma.sync m16n8k16.  k-step s, lane (g, t): logical
+// k = 2t, 2t+1 are physical CPL*t + 4s + {0, 1}; k = 2t+8, 2t+9 are
+// CPL*t + 4s + {2, 3}.
+template <int K>
+struct Prod<K, MATH_BF16> {
+  static constexpr int CPL = K / 4;
+  static constexpr int NT = K / 8;
+  static constexpr int KS = K / 16;
+  static constexpr int WORDS = NT * KS * 32 * 2;
+  __device__ static void fill(float *tabf, const float *__restrict__ Bn, int J, int R, int which) {
+    uint32_t *tab = reinterpret_cast<uint32_t *>(tabf);
+    for (int e = threadIdx.x; e < NT * KS * 32; e += blockDim.x) {
+      const int lane = e & 31, us = e >> 5, s = us % KS, u = us / KS;
+      const int g = lane >> 2, t = lane & 3;
+      const int col = out_col<K>(u, g);
+      const int k0 = CPL * t + 4 * s;
+      tab[2 * e] = pack_bf16(core_entry(Bn, J, R, which, k0, col), core_entry(Bn, J, R, which, k0 + 1, col));
+      tab[2 * e + 1] =
+          pack_bf16(core_entry(Bn, J, R, which, k0 + 2, col), core_entry(Bn, J, R, which, k0 + 3, col));
+    }
+  }
+  __device__ static void run(const float (&x)[2][CPL], const float *tabf, float (&y)[2][CPL], int lane) {
+    const uint2 *tab = reinterpret_cast<const uint2 *>(tabf);
+    uint32_t xa[2][CPL / 2];
+#pragma unroll
+    for (int q = 0; q < CPL / 2; ++q) {
+      xa[0][q] = pack_bf16(x[0][2 * q], x[0][2 * q + 1]);
+      xa[1][q] = pack_bf16(x[1][2 * q], x[1][2 * q + 1]);
+    }
+#pragma unroll
+    for (int u = 0; u < NT; ++u) {
+      float acc[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+      for (int s = 0; s < KS; ++s) {
+        const uint2 b = tab[(u * KS + s) * 32 + lane];
+        mma_bf16(acc, xa[0][2 * s], xa[1][2 * s], xa[0][2 * s + 1], xa[1][2 * s + 1], b.x, b.y);
+      }
+      y[0][2 * u] = acc[0]; y[0][2 * u + 1] = acc[1];
+      y[1][2 * u] = acc[2]; y[1][2 * u + 1] = acc[3];
+    }
+  }
+};
+
+// ---------------------------------------------------------- row-chunk I/O
+// Read the lane's chunk of factor row `row` (zeros past J_n or when !valid).
+// In the factor phase rows are read at L2 (ld.global.cg) because other warps
+// write them during the pass; the core phase may use the read-only path.
+template <int K, bool READ_ONLY>
+__device__ __forceinline__ void load_chunk(const float *__restrict__ An, int64_t row, int J, int t,
+                                           bool valid, bool vec, float (&v)[K / 4]) {
+  constexpr int CPL = K / 4;
+  if (!valid) {
+#pragma unroll
+    for (int q = 0; q < CPL; ++q) v[q] = 0.f;
+    return;
+  }
+  const float *p = An + row * J + CPL * t;
+  if (vec) {
+#pragma unroll
+    for (int w = 0; w < CPL; w += 4) {
+      float4 f;
+      if constexpr (READ_ONLY) f = __ldg(reinterpret_cast<const float4 *>(p + w));
+      else f = __ldcg(reinterpret_cast<const float4 *>(p + w));
+      v[w] = f.x; v[w + 1] = f.y; v[w + 2] = f.z; v[w + 3] = f.w;
+    }
+  } else {
+#pragma unroll
+    for (int q = 0; q < CPL; ++q) {
+      const int j = CPL * t + q;
+      if (j < J) v[q] = READ_ONLY ? __ldg(p + q) : __ldcg(p + q);
+      else v[q] = 0.f;
+    }
+  }
+}
+
+template <int K>
+__device__ __forceinline__ void store_chunk(float *__restrict__ An, int64_t row, int J, int t, bool vec,
+                                            const float (&v)[K / 4]) {
+  constexpr int CPL = K / 4;
+  float *p = An + row * J + CPL * t;
+  if (vec) {
+#pragma unroll
+    for (int w = 0; w < CPL; w += 4) __stcg(reinterpret_cast<float4 *>(p + w), make_float4(v[w], v[w + 1], v[w + 2], v[w + 3]));
+  } else {
+#pragma unroll
+    for (int q = 0; q < CPL; ++q)
+      if (CPL * t + q < J) __stcg(p + q, v[q]);
+  }
+}
+
+// ------------------------------------------------------- shared tile front
+// Gathers the tile (a1, a2), forms C^(n) = A_Psi^(n) B^(n) for every mode
+// (Algorithm 4, C step) and the prediction xhat per row (Eq. "fasttucker").
+template <int N, int K, int MATH, bool READ_ONLY>
+struct Front {
+  static constexpr int CPL = K / 4;
+  int64_t m[2];
+  bool valid[2];
+  int32_t row[N][2];
+  float x[2];
+  float a[N][2][CPL];
+  float c[N][2][CPL];
+  float xhat[2];
+
+  __device__ __forceinline__ void load(const EpochArgs &p, int64_t tile_base, int lane, bool need_x) {
+    const int g = lane >> 2, t = lane & 3;
+    m[0] = tile_base + g;
+    m[1] = tile_base + g + 8;
+    valid[0] = m[0] < p.end;
+    valid[1] = m[1] < p.end;
+#pragma unroll
+    for (int n = 0; n < N; ++n)
+#pragma unroll
+      for (int h = 0; h < 2; ++h) row[n][h] = valid[h] ? __ldcs(p.idx[n] + m[h]) : 0;
+    // a coordinate outside [0, I_n) masks its nonzero and latches an error
+    bool bad = false;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      bool ok = true;
+#pragma unroll
+      for (int n = 0; n < N; ++n) ok = ok && row[n][h] >= 0 && int64_t(row[n][h]) < p.I[n];
+      if (valid[h] && !ok) {
+        bad = true;
+        valid[h] = false;
+#pragma unroll
+        for (int n = 0; n < N; ++n) row[n][h] = 0;
+      }
+    }
+    if (bad) atomicOr(p.err, ERRBIT_INDEX);
+#pragma unroll
+    for (int h = 0; h < 2; ++h) x[h] = (need_x && valid[h]) ? __ldcs(p.vals + m[h]) : 0.f;
+#pragma unroll
+    for (int n = 0; n < N; ++n)
+#pragma unroll
+      for (int h = 0; h < 2; ++h)
+        load_chunk<K, READ_ONLY>(p.A[n], row[n][h], p.J[n], t, valid[h], (p.vecmask >> n) & 1, a[n][h]);
+  }
+
+  __device__ __forceinline__ void compute(const float *tabB, int tab_words, int lane) {
+    // tabB: table of product a.B of mode n at tabB + n * tab_words
+#pragma unroll
+    for (int n = 0; n < N; ++n) Prod<K, MATH>::run(a[n], tabB + n * tab_words, c[n], lane);
+    // xhat = sum_r prod_n c^(n)_r: lane partial over its chunk, then the group of four
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      float s = 0.f;
+#pragma unroll
+      for (int q = 0; q < CPL; ++q) {
+        float pr = c[0][h][q];
+#pragma unroll
+        for (int n = 1; n < N; ++n) pr *= c[n][h][q];
+        s += pr;
+      }
+      s += __shfl_xor_sync(FULL, s, 1);
+      s += __shfl_xor_sync(FULL, s, 2);
+      xhat[h] = s;
+    }
+  }
+
+  // D^(n) = prod_{k != n} C^(k) (Algorithm 4, Hadamard step)
+  __device__ __forceinline__ void leave_one_out(int n, float (&d)[2][CPL]) const {
+#pragma unroll
+    for (int h = 0; h < 2; ++h)
+#pragma unroll
+      for (int q = 0; q < CPL; ++q) {
+        float pr = 1.f;
+#pragma unroll
+        for (int k = 0; k < N; ++k)
+          if (k != n) pr *= c[k][h][q];
+        d[h][q] = pr;
+      }
+  }
+};
+
+// Shared-memory table layout of the factor kernel: for each mode, the a.B
+// table, then for each mode the d.B^T table.
+template <int N, int K, int MATH>
+struct FactorSmem {
+  static constexpr int TW = Prod<K, MATH>::WORDS;
+  static constexpr size_t bytes() { return size_t(2) * N * TW * sizeof(float); }
+};
+
+template <int N, int K, int MATH>
+__device__ __forceinline__ void fill_tables(float *smem, const EpochArgs &p, bool both) {
+  constexpr int TW = Prod<K, MATH>::WORDS;
+#pragma unroll 1
+  for (int n = 0; n < N; ++n) {
+    Prod<K, MATH>::fill(smem + n * TW, p.B[n], p.J[n], p.R, 0);
+    if (both) Prod<K, MATH>::fill(smem + (N + n) * TW, p.B[n], p.J[n], p.R, 1);
+  }
+}
+
+// ------------------------------------------------------------- factor phase
+// One pass of the factor update over [begin, end) (Algorithm 4):
+//   C = A_Psi B, D = *_{k != n} C, P = D B^T, e = x - xhat,
+//   a <- a + lr * s_row * (e P - lam a)   (Eq. "Update_FastTuckerPlus_factor")
+// DELTA = false: rows are stored back at once (Hogwild, as in the paper).
+// DELTA = true: the per-nonzero step e P - lam a is written to p.delta for the
+// deterministic batch reduction; A is not modified.
+template <int N, int K, int MATH, bool DELTA>
+__global__ void __launch_bounds__(256) k_factor(const EpochArgs p) {
+  extern __shared__ __align__(16) float smem[];
+  constexpr int CPL = K / 4;
+  constexpr int TW = Prod<K, MATH>::WORDS;
+  fill_tables<N, K, MATH>(smem, p, true);
+  __syncthreads();
+
+  const int lane = threadIdx.x & 31;
+  const int t = lane & 3;
+  const int64_t warp = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = (int64_t(gridDim.x) * blockDim.x) >> 5;
+  const int64_t ntiles = (p.end - p.begin + FT_TILE - 1) / FT_TILE;
+
+  for (int64_t tile = warp; tile < ntiles; tile += nwarps) {
+    Front<N, K, MATH, false> f;
+    f.load(p, p.begin + tile * FT_TILE, lane, true);
+    f.compute(smem, TW, lane);
+    float e[2];
+    e[0] = f.x[0] - f.xhat[0];
+    e[1] = f.x[1] - f.xhat[1];
+    const bool bad = (f.valid[0] && !isfinite(e[0])) || (f.valid[1] && !isfinite(e[1]));
+    if (__any_sync(FULL, bad) && lane == 0) atomicOr(p.err, ERRBIT_NONFINITE);
+#pragma unroll
+    for (int n = 0; n < N; ++n) {
+      float d[2][CPL], pp[2][CPL];
+      f.leave_one_out(n, d);
+      Prod<K, MATH>::run(d, smem + (N + n) * TW, pp, lane);
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        if (!f.valid[h]) continue;
+        float out[CPL];
+        if constexpr (DELTA) {
+#pragma unroll
+          for (int q = 0; q < CPL; ++q) out[q] = e[h] * pp[h][q] - p.lam * f.a[n][h][q];
+          float *dst = p.delta + (f.m[h] - p.begin) * p.sumJ + p.offJ[n] + CPL * t;
+#pragma unroll
+          for (int q = 0; q < CPL; ++q)
+            if (CPL * t + q < p.J[n]) dst[q] = out[q];
+        } else {
+          const float lr = p.scale[n] ? p.lr * __ldg(p.scale[n] + f.row[n][h]) : p.lr;
+#pragma unroll
+          for (int q = 0; q < CPL; ++q)
+            out[q] = fmaf(lr, fmaf(e[h], pp[h][q], -p.lam * f.a[n][h][q]), f.a[n][h][q]);
+          store_chunk<K>(p.A[n], f.row[n][h], p.J[n], t, (p.vecmask >> n) & 1, out);
+        }
+      }
+    }
+  }
+}
+
+// --------------------------------------------------------------- core phase
+// Per tile: E^(n) = (xhat - x) * A_Psi^(n), G^(n) += E^(n)T D^(n) (Algorithm 5).
+// The 16 x K operands are staged in the warp's shared memory so that the
+// contraction over the tile's nonzeros can run on the tensor cores; the
+// tile results are added with Neumaier compensation into per-warp float
+// accumulators (lane-private slots), combined per CTA in warp order and
+// written as one (sum, compensation) partial per CTA.  Fixed grid and static
+// tile order make the result reproducible bit for bit.
+//
+// Accumulator slot q of a lane (q < K*K/32): q = (mt * (K/8) + u) * 4 + i is
+// element (j, r) = (16 mt + g + 8 (i / 2), 8 u + 2 t + i % 2) of G^(n).
+template <int K, int MATH>
+struct GradTile {
+  static constexpr int LD = (MATH == MATH_BF16) ? K + 4 : K + 8;  // conflict-free strides
+  static constexpr int SLOTS = K * K / 32;
+  __device__ static void run(const float *Es, const float *Ds, float (&out)[SLOTS], int lane) {
+    const int g = lane >> 2, t = lane & 3;
+#pragma unroll
+    for (int mt = 0; mt < K / 16; ++mt)
+#pragma unroll
+      for (int u = 0; u < K / 8; ++u) {
+        float acc[4] = {0.f, 0.f, 0.f, 0.f};
+        const int j0 = 16 * mt + g, r0 = 8 * u + g;
+        if constexpr (MATH == MATH_TF32) {
+#pragma unroll
+          for (int s = 0; s < 2; ++s) {
+            const int m0 = 8 * s + t, m1 = m0 + 4;
+            mma_tf32(acc, to_tf32(Es[m0 * LD + j0]), to_tf32(Es[m0 * LD + j0 + 8]), to_tf32(Es[m1 * LD + j0]),
+                     to_tf32(Es[m1 * LD + j0 + 8]), to_tf32(Ds[m0 * LD + r0]), to_tf32(Ds[m1 * LD + r0]));
+          }
+        } else if constexpr (MATH == MATH_BF16) {
+          const int m0 = 2 * t, m2 = 2 * t + 8;
+          mma_bf16(acc, pack_bf16(Es[m0 * LD + j0], Es[(m0 + 1) * LD + j0]),
+                   pack_bf16(Es[m0 * LD + j0 + 8], Es[(m0 + 1) * LD + j0 + 8]),
+                   pack_bf16(Es[m2 * LD + j0], Es[(m2 + 1) * LD + j0]),
+                   pack_bf16(Es[m2 * LD + j0 + 8], Es[(m2 + 1) * LD + j0 + 8]),
+                   pack_bf16(Ds[m0 * LD + r0], Ds[(m0 + 1) * LD + r0]),
+                   pack_bf16(Ds[m2 * LD + r0], Ds[(m2 + 1) * LD + r0]));
+        } else {
+#pragma unroll
+          for (int i = 0; i < 4; ++i) {
+            const int j = 16 * mt + g + 8 * (i >> 1), r = 8 * u + 2 * t + (i & 1);
+            float s = 0.f;
+#pragma unroll
+            for (int mm = 0; mm < FT_TILE; ++mm) s = fmaf(Es[mm * LD + j], Ds[mm * LD + r], s);
+            acc[i] = s;
+          }
+        }
+#pragma unroll
+        for (int i = 0; i < 4; ++i) out[(mt * (K / 8) + u) * 4 + i] = acc[i];
+      }
+  }
+};
+
+__device__ __forceinline__ void neumaier_add(float &sum, float &comp, float v) {
+  const float t = sum + v;
+  if (fabsf(sum) >= fabsf(v)) comp += (sum - t) + v;
+  else comp += (v - t) + sum;
+  sum = t;
+}
+
+template <int N, int K, int MATH>
+struct CoreSmem {
+  static constexpr int TW = Prod<K, MATH>::WORDS;
+  static constexpr int LD = GradTile<K, MATH>::LD;
+  static constexpr int STAGE = 2 * FT_TILE * LD;          // floats per warp (E and D)
+  static constexpr int ACC = 2 * N * K * K;               // floats per warp (sum and comp)
+  static constexpr int WARPS = (N * K * K > 2048) ? 4 : 8;
+  static constexpr size_t bytes() {
+    return sizeof(float) * (size_t(N) * TW + size_t(WARPS) * (STAGE + ACC));
+  }
+};
+
+template <int N, int K, int MATH>
+__global__ void __launch_bounds__(256) k_core(const EpochArgs p) {
+  extern __shared__ __align__(16) float smem[];
+  using L = CoreSmem<N, K, MATH>;
+  constexpr int CPL = K / 4;
+  constexpr int TW = L::TW;
+  constexpr int LD = L::LD;
+  constexpr int SL = GradTile<K, MATH>::SLOTS;
+  fill_tables<N, K, MATH>(smem, p, false);
+  const int warp_in_cta = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31;
+  const int g = lane >> 2, t = lane & 3;
+  float *stage = smem + N * TW + warp_in_cta * (L::STAGE + L::ACC);
+  float *Es = stage, *Ds = stage + FT_TILE * LD;
+  float *acc_s = stage + L::STAGE;            // [N][SL][32]
+  float *acc_c = acc_s + N * SL * 32;
+  for (int q = lane; q < N * SL * 32; q += 32) { acc_s[q] = 0.f; acc_c[q] = 0.f; }
+  __syncthreads();
+
+  const int64_t warp = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = (int64_t(gridDim.x) * blockDim.x) >> 5;
+  const int64_t ntiles = (p.end - p.begin + FT_TILE - 1) / FT_TILE;
+  for (int64_t tile = warp; tile < ntiles; tile += nwarps) {
+    Front<N, K, MATH, true> f;
+    f.load(p, p.begin + tile * FT_TILE, lane, true);
+    f.compute(smem, TW, lane);
+    const float ne0 = f.xhat[0] - f.x[0], ne1 = f.xhat[1] - f.x[1];
+#pragma unroll
+    for (int n = 0; n < N; ++n) {
+      float d[2][CPL];
+      f.leave_one_out(n, d);
+      // stage E = (xhat - x) * A_Psi and D, rows g and g + 8, the lane's chunk
+#pragma unroll
+      for (int q = 0; q < CPL; ++q) {
+        Es[g * LD + CPL * t + q] = ne0 * f.a[n][0][q];
+        Es[(g + 8) * LD + CPL * t + q] = ne1 * f.a[n][1][q];
+        Ds[g * LD + CPL * t + q] = d[0][q];
+        Ds[(g + 8) * LD + CPL * t + q] = d[1][q];
+      }
+      __syncwarp();
+      float part[SL];
+      GradTile<K, MATH>::run(Es, Ds, part, lane);
+      __syncwarp();
+#pragma unroll
+      for (int q = 0; q < SL; ++q) {
+        const int o = (n * SL + q) * 32 + lane;
+        float s = acc_s[o], c = acc_c[o];
+        neumaier_add(s, c, part[q]);
+        acc_s[o] = s;
+        acc_c[o] = c;
+      }
+    }
+  }
+  __syncthreads();
+  // CTA combine in warp order; partial layout [cta][n][K][K] of (sum, comp)
+  const int nw = blockDim.x >> 5;
+  float *out = p.partial + size_t(blockIdx.x) * 2 * N * K * K;
+  for (int f = threadIdx.x; f < N * SL * 32; f += blockDim.x) {
+    float s = 0.f, c = 0.f;
+    for (int w = 0; w < nw; ++w) {
+      const float *ws = smem + N * TW + w * (L::STAGE + L::ACC) + L::STAGE;
+      neumaier_add(s, c, ws[f]);
+      c += ws[N * SL * 32 + f];
+    }
+    const int ln = f & 31, q = (f >> 5) % SL, n = f / (SL * 32);
+    const int gg = ln >> 2, tt = ln & 3;
+    const int i = q & 3, u = (q >> 2) % (K / 8), mt = (q >> 2) / (K / 8);
+    const int j = 16 * mt + gg + 8 * (i >> 1), r = 8 * u + 2 * tt + (i & 1);
+    const size_t o = (size_t(n) * K + j) * K + r;
+    out[2 * o] = s;
+    out[2 * o + 1] = c;
+  }
+}
+
+// ----------------------------------------------------- predict and errors
+// FP32 predictions on the CUDA cores (the tensor-core modes only change the
+// epochs).  MODE 0: write xhat; MODE 1: per-CTA float64 sums of e^2 and |e|.
+template <int N, int K, int MODE>
+__global__ void __launch_bounds__(256) k_eval(const EpochArgs p) {
+  extern __shared__ __align__(16) float smem[];
+  constexpr int TW = Prod<K, MATH_FP32>::WORDS;
+  fill_tables<N, K, MATH_FP32>(smem, p, false);
+  __shared__ double red[2][8];
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = (int64_t(gridDim.x) * blockDim.x) >> 5;
+  const int64_t ntiles = (p.end - p.begin + FT_TILE - 1) / FT_TILE;
+  double se = 0.0, ae = 0.0;
+  for (int64_t tile = warp; tile < ntiles; tile += nwarps) {
+    Front<N, K, MATH_FP32, true> f;
+    f.load(p, p.begin + tile * FT_TILE, lane, MODE == 1);
+    f.compute(smem, TW, lane);
+    if ((lane & 3) == 0) {
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        if (!f.valid[h]) continue;
+        if constexpr (MODE == 0) {
+          p.pred[f.m[h] - p.begin] = f.xhat[h];
+        } else {
+          const float e = f.x[h] - f.xhat[h];
+          if (!isfinite(e)) atomicOr(p.err, ERRBIT_NONFINITE);
+          se += double(e) * double(e);
+          ae += fabs(double(e));
+        }
+      }
+    }
+  }
+  if constexpr (MODE == 1) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      se += __shfl_xor_sync(FULL, se, o);
+      ae += __shfl_xor_sync(FULL, ae, o);
+    }
+    const int w = threadIdx.x >> 5;
+    if (lane == 0) { red[0][w] = se; red[1][w] = ae; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double a = 0.0, b = 0.0;
+      for (int i = 0; i < (int)(blockDim.x >> 5); ++i) { a += red[0][i]; b += red[1][i]; }
+      p.err_partial[2 * blockIdx.x] = a;
+      p.err_partial[2 * blockIdx.x + 1] = b;
+    }
+  }
+}
+
+}  // namespace ft

@@ -1,0 +1,261 @@
+"""Thin ctypes binding of the C ABI in ``include/ft.h``.
+
+The functions below carry the C names and only marshal arguments (device
+pointers from torch tensors, host arrays of pointers, the current stream);
+every step of the epoch runs in the CUDA library.  There is no fallback: if
+``_build/libft.so`` is missing or cannot be loaded, ``load()`` raises.
+
+``FastTuckerPlus`` is a small convenience wrapper that owns the workspace
+(a torch byte tensor) and keeps the borrowed tensors alive.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import torch
+
+from . import _build
+
+FT_FP32, FT_TF32, FT_BF16 = 0, 1, 2
+FT_HOGWILD, FT_DETERMINISTIC = 0, 1
+PRECISIONS = {"fp32": FT_FP32, "tf32": FT_TF32, "bf16": FT_BF16}
+SCATTERS = {"hogwild": FT_HOGWILD, "deterministic": FT_DETERMINISTIC}
+
+FT_OK = 0
+STATUS = {0: "FT_OK", -1: "FT_ERR_ARG", -2: "FT_ERR_INDEX", -3: "FT_ERR_SHAPE", -4: "FT_ERR_CUDA",
+          -5: "FT_ERR_NONFINITE", -6: "FT_ERR_TIMEOUT", -7: "FT_ERR_WORKSPACE"}
+
+# Every symbol the header declares (checked by the tests against the library).
+EXPORTS = ["ft_config_default", "ft_workspace_size", "ft_init", "ft_epoch_factors",
+           "ft_epoch_core", "ft_core_grad", "ft_predict", "ft_rmse", "ft_check",
+           "ft_launch_count", "ft_destroy", "ft_status_str"]
+
+
+class FtError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        super().__init__(f"{where}: {STATUS.get(status, status)}")
+
+
+class ft_config(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int), ("scatter", ctypes.c_int),
+                ("det_batch", ctypes.c_int64), ("blocks_per_sm", ctypes.c_int),
+                ("reserved", ctypes.c_int * 7)]
+
+
+_lib = None
+_lock = threading.Lock()
+_P = ctypes.c_void_p
+
+
+def library_path() -> str:
+    return _build.LIB_PATH
+
+
+def load(path: str | None = None):
+    """Load the CUDA library (no build, no fallback)."""
+    global _lib
+    with _lock:
+        if _lib is not None and path is None:
+            return _lib
+        p = path or _build.LIB_PATH
+        if not os.path.exists(p):
+            raise ImportError(f"CUDA library not built: {p} is missing (run __graft_entry__.build())")
+        lib = ctypes.CDLL(p)
+        _declare(lib)
+        if path is None:
+            _lib = lib
+        return lib
+
+
+def _declare(lib):
+    I64, INT, FLT = ctypes.c_int64, ctypes.c_int, ctypes.c_float
+    sigs = {
+        "ft_config_default": (None, [_P]),
+        "ft_workspace_size": (INT, [INT, _P, _P, INT, I64, _P, _P]),
+        "ft_init": (INT, [_P, INT, _P, _P, INT, I64, _P, _P, _P, _P, _P, ctypes.c_size_t, _P, _P]),
+        "ft_epoch_factors": (INT, [_P, FLT, FLT, _P, _P]),
+        "ft_epoch_core": (INT, [_P, FLT, FLT, _P]),
+        "ft_core_grad": (INT, [_P, _P, _P]),
+        "ft_predict": (INT, [_P, I64, _P, _P, _P]),
+        "ft_rmse": (INT, [_P, I64, _P, _P, _P, _P]),
+        "ft_check": (INT, [_P, _P]),
+        "ft_launch_count": (I64, [_P]),
+        "ft_destroy": (None, [_P]),
+        "ft_status_str": (ctypes.c_char_p, [INT]),
+    }
+    for name, (res, args) in sigs.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+
+
+def _check(status: int, where: str):
+    if status != FT_OK:
+        raise FtError(status, where)
+
+
+def _ptrs(tensors, ctype=ctypes.c_void_p):
+    return (ctype * len(tensors))(*[0 if t is None else t.data_ptr() for t in tensors])
+
+
+def _stream(stream) -> int:
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+
+
+def make_config(precision="fp32", scatter="hogwild", det_batch=4096, blocks_per_sm=0) -> ft_config:
+    c = ft_config()
+    load().ft_config_default(ctypes.byref(c))
+    c.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+    c.scatter = SCATTERS[scatter] if isinstance(scatter, str) else int(scatter)
+    c.det_batch = int(det_batch)
+    c.blocks_per_sm = int(blocks_per_sm)
+    return c
+
+
+# ------------------------------------------------------ C-named functions
+def ft_workspace_size(I, J, R, nnz, cfg: ft_config) -> int:
+    N = len(I)
+    Ia = (ctypes.c_int64 * N)(*[int(v) for v in I])
+    Ja = (ctypes.c_int * N)(*[int(v) for v in J])
+    out = ctypes.c_size_t(0)
+    _check(load().ft_workspace_size(N, Ia, Ja, int(R), int(nnz), ctypes.byref(cfg), ctypes.byref(out)),
+           "ft_workspace_size")
+    return int(out.value)
+
+
+def ft_init(I, J, R, idx, vals, A, B, workspace, cfg: ft_config, stream=None):
+    """idx, A, B: lists of device tensors (int32 / float32); returns the
+    context handle (an int)."""
+    N = len(I)
+    Ia = (ctypes.c_int64 * N)(*[int(v) for v in I])
+    Ja = (ctypes.c_int * N)(*[int(v) for v in J])
+    nnz = int(vals.numel())
+    ctx = ctypes.c_void_p(0)
+    _check(load().ft_init(ctypes.byref(ctx), N, Ia, Ja, int(R), nnz, _ptrs(idx), vals.data_ptr(),
+                          _ptrs(A), _ptrs(B), workspace.data_ptr(), workspace.numel() * workspace.element_size(),
+                          ctypes.byref(cfg), _stream(stream)), "ft_init")
+    return ctx.value
+
+
+def ft_epoch_factors(ctx, lr_a, lambda_a, row_step_scale=None, stream=None):
+    scale = None if row_step_scale is None else _ptrs(row_step_scale)
+    _check(load().ft_epoch_factors(ctx, float(lr_a), float(lambda_a), scale, _stream(stream)),
+           "ft_epoch_factors")
+
+
+def ft_epoch_core(ctx, lr_b, lambda_b, stream=None):
+    _check(load().ft_epoch_core(ctx, float(lr_b), float(lambda_b), _stream(stream)), "ft_epoch_core")
+
+
+def ft_core_grad(ctx, G_out, stream=None):
+    _check(load().ft_core_grad(ctx, G_out.data_ptr(), _stream(stream)), "ft_core_grad")
+
+
+def ft_predict(ctx, idx, out, stream=None):
+    n = int(out.numel())
+    _check(load().ft_predict(ctx, n, _ptrs(idx) if n else None, out.data_ptr() if n else None,
+                             _stream(stream)), "ft_predict")
+
+
+def ft_rmse(ctx, idx, vals, stream=None):
+    """Returns (rmse, mae, sum of squared errors); synchronises the stream."""
+    n = int(vals.numel())
+    out = (ctypes.c_double * 3)()
+    _check(load().ft_rmse(ctx, n, _ptrs(idx) if n else None, vals.data_ptr() if n else None, out,
+                          _stream(stream)), "ft_rmse")
+    return float(out[0]), float(out[1]), float(out[2])
+
+
+def ft_check(ctx, stream=None):
+    _check(load().ft_check(ctx, _stream(stream)), "ft_check")
+
+
+def ft_launch_count(ctx) -> int:
+    return int(load().ft_launch_count(ctx))
+
+
+def ft_destroy(ctx):
+    if ctx:
+        load().ft_destroy(ctx)
+
+
+def ft_status_str(status: int) -> str:
+    return load().ft_status_str(int(status)).decode()
+
+
+# ----------------------------------------------------------- convenience
+class FastTuckerPlus:
+    """One sparse tensor's training context.
+
+    idx: list of N int32 device tensors (nnz,), vals: float32 (nnz,),
+    A: list of N float32 (I_n, J_n), B: list of N float32 (J_n, R), all on
+    the same CUDA device and contiguous.  A and B are updated in place.
+    """
+
+    def __init__(self, idx, vals, A, B, precision="fp32", scatter="hogwild", det_batch=4096,
+                 blocks_per_sm=0, stream=None):
+        N = len(A)
+        if not (len(idx) == len(B) == N):
+            raise ValueError("idx, A and B need one entry per mode")
+        for t in list(idx) + [vals] + list(A) + list(B):
+            if not t.is_cuda or not t.is_contiguous():
+                raise ValueError("every tensor must be a contiguous CUDA tensor")
+        self.idx = [t for t in idx]
+        self.vals = vals
+        self.A = list(A)
+        self.B = list(B)
+        self.I = [int(a.shape[0]) for a in A]
+        self.J = [int(a.shape[1]) for a in A]
+        self.R = int(B[0].shape[1])
+        self.nnz = int(vals.numel())
+        self.cfg = make_config(precision, scatter, det_batch, blocks_per_sm)
+        ws = ft_workspace_size(self.I, self.J, self.R, self.nnz, self.cfg)
+        self.workspace = torch.empty(max(ws, 256), dtype=torch.uint8, device=vals.device)
+        self.ctx = ft_init(self.I, self.J, self.R, self.idx, vals, self.A, self.B, self.workspace,
+                           self.cfg, stream)
+
+    def epoch_factors(self, lr, lam, row_step_scale=None, stream=None):
+        ft_epoch_factors(self.ctx, lr, lam, row_step_scale, stream)
+
+    def epoch_core(self, lr, lam, stream=None):
+        ft_epoch_core(self.ctx, lr, lam, stream)
+
+    def core_grad(self, stream=None):
+        G = torch.empty(sum(j * self.R for j in self.J), dtype=torch.float32, device=self.vals.device)
+        ft_core_grad(self.ctx, G, stream)
+        out, off = [], 0
+        for j in self.J:
+            out.append(G[off:off + j * self.R].view(j, self.R))
+            off += j * self.R
+        return out
+
+    def predict(self, idx, stream=None):
+        out = torch.empty(int(idx[0].numel()), dtype=torch.float32, device=self.vals.device)
+        ft_predict(self.ctx, idx, out, stream)
+        return out
+
+    def rmse(self, idx, vals, stream=None):
+        return ft_rmse(self.ctx, idx, vals, stream)
+
+    def check(self, stream=None):
+        ft_check(self.ctx, stream)
+
+    @property
+    def launches(self) -> int:
+        return ft_launch_count(self.ctx)
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            ft_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,62 @@
+"""Host-side checks of the C ABI: the library builds for sm_103a, loads
+without a GPU, and exports every function include/*.h declares."""
+import ctypes
+import glob
+import os
+import re
+
+import pytest
+
+from paper_2404_10087_gb300 import _build, ft
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        text = open(h).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        text = re.sub(r"//[^\n]*", "", text)
+        for m in re.finditer(r"\b(ft_[a-z0-9_]+)\s*\(", text):
+            names.add(m.group(1))
+    return names
+
+
+@pytest.fixture(scope="module")
+def lib():
+    path = _build.build()
+    return ctypes.CDLL(path)
+
+
+def test_header_declares_the_binding_surface():
+    assert declared_functions() == set(ft.EXPORTS)
+
+
+def test_library_exports_every_declared_symbol(lib):
+    missing = [n for n in declared_functions() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_host_only_calls_without_gpu():
+    lib = ft.load()
+    cfg = ft.ft_config()
+    lib.ft_config_default(ctypes.byref(cfg))
+    assert cfg.precision == ft.FT_FP32 and cfg.scatter == ft.FT_HOGWILD and cfg.det_batch == 4096
+    assert ft.ft_status_str(0) == "ok"
+    assert ft.ft_status_str(-2) == "coordinate out of range"
+    lib.ft_destroy(None)
+    assert lib.ft_launch_count(None) == 0
+
+
+def test_shape_rejection_before_any_device_call():
+    """Unsupported shapes are refused on the host (no device query needed)."""
+    cfg = ft.make_config()
+    for I, J, R in [((10,) * 9, (4,) * 9, 4),       # N > 8
+                    ((10, 10), (4, 33), 4),          # J > 32
+                    ((10, 10), (4, 4), 33),          # R > 32
+                    ((10,) * 5, (32,) * 5, 8),       # N * K > 128
+                    ((10, 10), (0, 4), 4)]:          # J < 1
+        with pytest.raises(ft.FtError) as e:
+            ft.ft_workspace_size(I, J, R, 100, cfg)
+        assert e.value.status == -3

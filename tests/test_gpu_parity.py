@@ -1,0 +1,273 @@
+"""GPU path against the FP64 oracle, through the C ABI.
+
+Tolerances (relative; denominators as stated):
+  * FP32 path: predictions and per-element core gradients <= 1e-5 with the
+    denominator max(|ref|, 1e-3 * RMS(ref)); one deterministic factor
+    epoch's factors <= 1e-4 (Frobenius per matrix) and its step
+    A_new - A_old <= 1e-4; one core epoch's B <= 1e-5.
+  * TF32 path: steps and gradients <= 5e-3 (Frobenius).
+  * BF16 path: steps and gradients <= 2e-2 (Frobenius).
+Sizes span several 16-nonzero tiles with a ragged tail.
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2404_10087_gb300 import ft, synth
+
+pytestmark = pytest.mark.gpu
+
+DEV = "cuda:0"
+TOL_STEP = {"fp32": 1e-4, "tf32": 5e-3, "bf16": 2e-2}
+TOL_GRAD = {"fp32": 1e-5, "tf32": 5e-3, "bf16": 2e-2}
+
+
+def to_dev(idx, x, A, B):
+    return ([idx[n].contiguous().to(DEV) for n in range(idx.shape[0])], x.to(DEV),
+            [a.clone().to(DEV) for a in A], [b.clone().to(DEV) for b in B])
+
+
+def f64(ts):
+    return [t.detach().double().cpu().numpy() for t in ts]
+
+
+def rel_elem(got, ref):
+    got, ref = np.asarray(got, np.float64), np.asarray(ref, np.float64)
+    rms = math.sqrt(float(np.mean(ref * ref))) if ref.size else 0.0
+    den = np.maximum(np.abs(ref), 1e-3 * rms + 1e-300)
+    return float(np.max(np.abs(got - ref) / den)) if ref.size else 0.0
+
+
+def rel_fro(got, ref):
+    got, ref = np.asarray(got, np.float64), np.asarray(ref, np.float64)
+    d = np.linalg.norm(ref)
+    return float(np.linalg.norm(got - ref) / d) if d > 0 else float(np.linalg.norm(got))
+
+
+SHAPES = [
+    # (I, J, R, nnz)
+    ((50, 60, 70), (16, 16, 16), 16, 16 * 37 + 5),
+    ((40, 50, 60), (4, 5, 6), 7, 1000),
+    ((30, 20), (3, 9), 11, 333),
+    ((25,), (8,), 5, 77),
+    ((20, 21, 22, 23), (32, 32, 32, 32), 32, 16 * 20 + 9),
+    ((20, 21, 22, 23, 24), (16, 12, 10, 8, 16), 16, 400),
+    ((9, 10, 11, 12, 13, 14, 15, 16), (4, 4, 4, 4, 4, 4, 4, 4), 4, 300),
+    ((40, 40, 40), (20, 24, 17), 29, 700),
+]
+SHAPE_IDS = [f"N{len(s[0])}_J{max(s[1])}_R{s[2]}_nnz{s[3]}" for s in SHAPES]
+
+
+@pytest.mark.parametrize("shape", SHAPES, ids=SHAPE_IDS)
+def test_predict_fp32(shape):
+    I, J, R, nnz = shape
+    idx, x, A, B = synth.random_problem(1, I, J, R, nnz)
+    gidx, gx, gA, gB = to_dev(idx, x, A, B)
+    m = ft.FastTuckerPlus(gidx, gx, gA, gB)
+    got = m.predict(gidx).double().cpu().numpy()
+    ref = oracle.predict(f64(A), f64(B), idx.numpy())
+    assert rel_elem(got, ref) <= 1e-5
+
+
+@pytest.mark.parametrize("precision", ["fp32", "tf32", "bf16"])
+@pytest.mark.parametrize("shape", SHAPES, ids=SHAPE_IDS)
+def test_deterministic_factor_epoch(shape, precision):
+    I, J, R, nnz = shape
+    idx, x, A, B = synth.random_problem(2, I, J, R, nnz)
+    gidx, gx, gA, gB = to_dev(idx, x, A, B)
+    S = 128
+    lr, lam = 0.02, 0.05
+    m = ft.FastTuckerPlus(gidx, gx, gA, gB, precision=precision, scatter="deterministic", det_batch=S)
+    m.epoch_factors(lr, lam)
+    m.check()
+    ref = oracle.factor_epoch(f64(A), f64(B), idx.numpy(), x.double().numpy(), S, lr, lam)
+    got = f64(gA)
+    A0 = f64(A)
+    for n in range(len(I)):
+        if precision == "fp32":
+            assert rel_fro(got[n], ref[n]) <= 1e-4
+        assert rel_fro(got[n] - A0[n], ref[n] - A0[n]) <= TOL_STEP[precision], n
+
+
+@pytest.mark.parametrize("precision", ["fp32", "tf32", "bf16"])
+@pytest.mark.parametrize("shape", SHAPES, ids=SHAPE_IDS)
+def test_core_gradient(shape, precision):
+    I, J, R, nnz = shape
+    idx, x, A, B = synth.random_problem(3, I, J, R, nnz)
+    gidx, gx, gA, gB = to_dev(idx, x, A, B)
+    m = ft.FastTuckerPlus(gidx, gx, gA, gB, precision=precision)
+    G = f64(m.core_grad())
+    ref = oracle.core_grad(f64(A), f64(B), idx.numpy(), x.double().numpy())
+    for n in range(len(I)):
+        if precision == "fp32":
+            assert rel_elem(G[n], ref[n]) <= 1e-5, n
+        assert rel_fro(G[n], ref[n]) <= TOL_GRAD[precision], n
+
+
+@pytest.mark.parametrize("precision", ["fp32", "bf16"])
+def test_core_epoch_and_errors(precision):
+    I, J, R, nnz = (60, 70, 80), (16, 16, 16), 16, 5000
+    idx, x, A, B = synth.random_problem(4, I, J, R, nnz)
+    gidx, gx, gA, gB = to_dev(idx, x, A, B)
+    m = ft.FastTuckerPlus(gidx, gx, gA, gB, precision=precision)
+    lr, lam = 0.5, 0.01
+    m.epoch_core(lr, lam)
+    ref = oracle.core_epoch(f64(A), f64(B), idx.numpy(), x.double().numpy(), lr, lam)
+    got = f64(gB)
+    B0 = f64(B)
+    for n in range(3):
+        assert rel_fro(got[n] - B0[n], ref[n] - B0[n]) <= TOL_GRAD[precision]
+    r = m.rmse(gidx, gx)
+    ro = oracle.errors(f64(gA), f64(gB), idx.numpy(), x.double().numpy())
+    assert abs(r[0] - ro[0]) <= 1e-5 * ro[0]
+    assert abs(r[1] - ro[1]) <= 1e-5 * ro[1]
+    assert abs(r[2] - ro[2]) <= 2e-5 * ro[2]
+
+
+def test_row_step_scale_deterministic():
+    I, J, R, nnz = (30, 40, 50), (16, 16, 16), 16, 900
+    idx, x, A, B = synth.random_problem(5, I, J, R, nnz)
+    gidx, gx, gA, gB = to_dev(idx, x, A, B)
+    g = torch.Generator().manual_seed(9)
+    scales = [torch.rand(In, generator=g, dtype=torch.float64).float() * 3.75 + 0.25 for In in I]
+    m = ft.FastTuckerPlus(gidx, gx, gA, gB, scatter="deterministic", det_batch=64)
+    m.epoch_factors(0.02, 0.05, [s.to(DEV) for s in scales])
+    ref = oracle.factor_epoch(f64(A), f64(B), idx.numpy(), x.double().numpy(), 64, 0.02, 0.05,
+                              row_scale=[s.double().numpy() for s in scales])
+    for n in range(3):
+        assert rel_fro(f64(gA)[n] - f64(A)[n], ref[n] - f64(A)[n]) <= 1e-4
+
+
+@pytest.mark.parametrize("precision", ["fp32", "tf32", "bf16"])
+def test_hogwild_without_collisions_is_exact(precision):
+    """When no two nonzeros share a row in any mode, the Hogwild pass has no
+    races and equals the sequential epoch."""
+    nnz = 16 * 50 + 3
+    I, J, R = (nnz + 5, nnz + 9, nnz), (16, 16, 16), 16
+    g = torch.Generator().manual_seed(6)
+    idx = torch.stack([torch.randperm(In, generator=g)[:nnz] for In in I]).to(torch.int32)
+    _, x, A, B = synth.random_problem(6, I, J, R, nnz)
+    gidx, gx, gA, gB = to_dev(idx, x, A, B)
+    m = ft.FastTuckerPlus(gidx, gx, gA, gB, precision=precision)
+    m.epoch_factors(0.03, 0.02)
+    m.check()
+    ref = oracle.factor_epoch(f64(A), f64(B), idx.numpy(), x.double().numpy(), 1, 0.03, 0.02)
+    for n in range(3):
+        assert rel_fro(f64(gA)[n] - f64(A)[n], ref[n] - f64(A)[n]) <= TOL_STEP[precision]
+
+
+def test_deterministic_mode_is_bitwise_reproducible():
+    I, J, R, nnz = (100, 20, 10), (16, 16, 16), 16, 4000
+    idx, x, A, B = synth.random_problem(7, I, J, R, nnz)
+    outs = []
+    for _ in range(2):
+        gidx, gx, gA, gB = to_dev(idx, x, A, B)
+        m = ft.FastTuckerPlus(gidx, gx, gA, gB, precision="bf16", scatter="deterministic", det_batch=512)
+        for _ in range(2):
+            m.epoch_factors(0.01, 0.01)
+            m.epoch_core(0.01, 0.01)
+        torch.cuda.synchronize()
+        outs.append([t.cpu() for t in gA + gB])
+    for a, b in zip(*outs):
+        assert torch.equal(a, b)
+
+
+def test_planted_training_tracks_oracle():
+    """Ten epochs on the planted 3-order workload (1e5 uniform coordinates,
+    planted J = R = 4 with noise 0.1): the Hogwild FP32 run and the sequential
+    oracle reach test RMSE within 2% of each other."""
+    w = synth.WORKLOADS["planted_uniform_1e5"]
+    d = synth.draw_workload(w)
+    planted = oracle.predict(f64(d.planted_A), f64(d.planted_B), d.idx.numpy())
+    x = (torch.from_numpy(planted) + d.noise.double()).float()
+    tr, te = d.train, d.test
+    A0, B0 = synth.initial_factors(w)
+    gA = [a.clone().to(DEV) for a in A0]
+    gB = [b.clone().to(DEV) for b in B0]
+    tri = [d.idx[n, tr].contiguous().to(DEV) for n in range(3)]
+    tei = [d.idx[n, te].contiguous().to(DEV) for n in range(3)]
+    m = ft.FastTuckerPlus(tri, x[tr].contiguous().to(DEV), gA, gB)
+    lr = lam = 0.01
+    oA, oB = f64(A0), f64(B0)
+    itr, ite = d.idx[:, tr].numpy(), d.idx[:, te].numpy()
+    xtr, xte = x[tr].double().numpy(), x[te].double().numpy()
+    for _ in range(10):
+        m.epoch_factors(lr, lam)
+        m.epoch_core(lr, lam)
+        oA = oracle.factor_epoch(oA, oB, itr, xtr, 1, lr, lam)
+        oB = oracle.core_epoch(oA, oB, itr, xtr, lr, lam, nthreads=oracle.default_threads())
+    g = m.rmse(tei, x[te].contiguous().to(DEV))[0]
+    o = oracle.errors(oA, oB, ite, xte)[0]
+    assert abs(g - o) <= 0.02 * o, (g, o)
+
+
+# ------------------------------------------------------------ edge cases
+def test_empty_tensor():
+    I, J, R = (5, 6, 7), (4, 4, 4), 4
+    idx, x, A, B = synth.random_problem(8, I, J, R, 0)
+    gidx = [torch.empty(0, dtype=torch.int32, device=DEV) for _ in range(3)]
+    gx = torch.empty(0, dtype=torch.float32, device=DEV)
+    gA = [a.clone().to(DEV) for a in A]
+    gB = [b.clone().to(DEV) for b in B]
+    for scatter in ("hogwild", "deterministic"):
+        m = ft.FastTuckerPlus(gidx, gx, gA, gB, scatter=scatter)
+        m.epoch_factors(0.1, 0.1)
+        m.check()
+        assert all(torch.equal(a.cpu(), b) for a, b in zip(gA, A))
+    m.epoch_core(0.1, 0.5)  # no data: only the regulariser acts
+    for b, b0 in zip(gB, B):
+        torch.testing.assert_close(b.cpu(), b0 * (1 - 0.1 * 0.5), rtol=1e-6, atol=1e-7)
+    assert m.rmse(gidx, gx) == (0.0, 0.0, 0.0)
+
+
+@pytest.mark.parametrize("nnz", [1, 15, 16, 17])
+def test_tiny_tensors(nnz):
+    I, J, R = (3, 4, 5), (16, 16, 16), 16
+    idx, x, A, B = synth.random_problem(9, I, J, R, nnz)
+    gidx, gx, gA, gB = to_dev(idx, x, A, B)
+    m = ft.FastTuckerPlus(gidx, gx, gA, gB, scatter="deterministic", det_batch=4)
+    m.epoch_factors(0.05, 0.1)
+    ref = oracle.factor_epoch(f64(A), f64(B), idx.numpy(), x.double().numpy(), 4, 0.05, 0.1)
+    for n in range(3):
+        assert rel_fro(f64(gA)[n], ref[n]) <= 1e-5
+
+
+def test_bad_inputs_are_rejected():
+    I, J, R, nnz = (10, 11, 12), (4, 4, 4), 4, 100
+    idx, x, A, B = synth.random_problem(10, I, J, R, nnz)
+    gidx, gx, gA, gB = to_dev(idx, x, A, B)
+    bad = [t.clone() for t in gidx]
+    bad[1][17] = 11  # == I_2
+    with pytest.raises(ft.FtError) as e:
+        ft.FastTuckerPlus(bad, gx, gA, gB)
+    assert e.value.status == -2
+    bad[1][17] = -1
+    with pytest.raises(ft.FtError) as e:
+        ft.FastTuckerPlus(bad, gx, gA, gB)
+    assert e.value.status == -2
+    gx2 = gx.clone()
+    gx2[3] = float("nan")
+    with pytest.raises(ft.FtError) as e:
+        ft.FastTuckerPlus(gidx, gx2, gA, gB)
+    assert e.value.status == -5
+    cfg = ft.make_config()
+    ws = torch.empty(256, dtype=torch.uint8, device=DEV)
+    with pytest.raises(ft.FtError) as e:
+        ft.ft_init(I, J, R, gidx, gx, gA, gB, ws, cfg)
+    assert e.value.status == -7
+
+
+def test_nonfinite_residual_is_latched():
+    I, J, R, nnz = (10, 11, 12), (4, 4, 4), 4, 100
+    idx, x, A, B = synth.random_problem(11, I, J, R, nnz)
+    gidx, gx, gA, gB = to_dev(idx, x, A, B)
+    m = ft.FastTuckerPlus(gidx, gx, gA, gB)
+    gB[0][0, 0] = float("inf")  # poisons every prediction that uses row 0 of B^(1)
+    m.epoch_factors(0.01, 0.01)
+    with pytest.raises(ft.FtError) as e:
+        m.check()
+    assert e.value.status == -5
+    m.check()  # the latch was cleared
