@@ -44,7 +44,7 @@ FALLBACK_HBM_GBS = 6800.0
 def algorithmic_bytes_factor(N, J):
     """Per nonzero: N int32 coordinates + one float32 value read, N factor rows
     read and written (float32)."""
-    return 4 * N + 4 + 8 * 4 * sum(J)
+    return 4 * N + 4 + 2 * 4 * sum(J)
 
 
 def peak_hbm():
@@ -94,7 +94,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", "100"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.thread = threading.Thread(target=self._read, daemon=True)
             self.thread.start()
@@ -164,7 +164,7 @@ def run_ours(args, rank, world, local_rank):
     dev = torch.device(f"cuda:{local_rank}")
     torch.cuda.set_device(dev)
     ft.load()
-    w, tri, trx, tei, tex, A, B = make_workload(dev)
+    w, tri, trx, tei, tex, A, B = make_workload(dev, args.nnz)
     N, J, R = w.N, list(w.J), w.R
     nnz_train, nnz_test = int(trx.numel()), int(tex.numel())
     stream = torch.cuda.current_stream(dev)
@@ -259,7 +259,7 @@ def run_ours(args, rank, world, local_rank):
         "dtype": {"fp32": "f32", "tf32": "tf32", "bf16": "bf16"}[args.precision],
         "data": "synthetic (seeded Zipf coordinates, planted-model ratings; Netflix-shaped)",
         "config": {
-            "workload": WORKLOAD, "N": N, "I": list(w.I), "J": J, "R": R,
+            "workload": WORKLOAD if args.nnz is None else f"{WORKLOAD} at {args.nnz} coordinates", "N": N, "I": list(w.I), "J": J, "R": R,
             "nnz_train": nnz_train, "nnz_test": nnz_test, "precision": args.precision,
             "scatter": "hogwild", "lr": LR, "lambda": LAM,
             "parallelism": "replicas" if world > 1 else "single",
@@ -350,13 +350,16 @@ def run_reference(args, rank, world):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--precision", choices=["fp32", "tf32", "bf16"], default="fp32")
     ap.add_argument("--cpu-sample", type=int, default=2_000_000)
     ap.add_argument("--ref-sample", type=int, default=1_000_000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--nnz", type=int, default=None,
+                    help="distinct coordinates drawn (default: the workload's 1e8); "
+                         "a smaller case of the same recipe, e.g. for profiling")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
 

@@ -39,7 +39,7 @@ def nvcc() -> str:
     return cand
 
 
-def _sources_digest() -> str:
+def _sources_digest(extra=()) -> str:
     h = hashlib.sha256()
     for name in sorted(os.listdir(CSRC)):
         with open(os.path.join(CSRC, name), "rb") as f:
@@ -47,27 +47,31 @@ def _sources_digest() -> str:
             h.update(f.read())
     with open(os.path.join(INCLUDE, "ft.h"), "rb") as f:
         h.update(f.read())
-    h.update(" ".join(ARCH + NVCC_FLAGS).encode())
+    h.update(" ".join(ARCH + NVCC_FLAGS + list(extra)).encode())
     return h.hexdigest()
 
 
-def build(force: bool = False, jobs: int | None = None, verbose: bool = False) -> str:
+def build(force: bool = False, jobs: int | None = None, verbose: bool = False,
+          extra_defines=(), out_dir: str | None = None) -> str:
     """Compile every unit (in parallel) and link ``libft.so``; skipped when the
-    sources are unchanged since the last build."""
-    os.makedirs(OUT_DIR, exist_ok=True)
-    stamp = os.path.join(OUT_DIR, "sources.sha256")
-    digest = _sources_digest()
-    if not force and os.path.exists(LIB_PATH) and os.path.exists(stamp):
+    sources are unchanged since the last build.  ``extra_defines`` and
+    ``out_dir`` build a variant elsewhere (e.g. another cache policy)."""
+    out_dir = out_dir or OUT_DIR
+    lib_path = os.path.join(out_dir, "libft.so")
+    os.makedirs(out_dir, exist_ok=True)
+    stamp = os.path.join(out_dir, "sources.sha256")
+    digest = _sources_digest(extra_defines)
+    if not force and os.path.exists(lib_path) and os.path.exists(stamp):
         with open(stamp) as f:
             if f.read().strip() == digest:
-                return LIB_PATH
+                return lib_path
     exe = nvcc()
     jobs = jobs or max(1, min(len(UNITS), os.cpu_count() or 1))
 
     def compile_unit(unit):
         src, defs, name = unit
-        obj = os.path.join(OUT_DIR, name + ".o")
-        cmd = [exe, *ARCH, *NVCC_FLAGS, *defs, "-c", os.path.join(CSRC, src), "-o", obj]
+        obj = os.path.join(out_dir, name + ".o")
+        cmd = [exe, *ARCH, *NVCC_FLAGS, *extra_defines, *defs, "-c", os.path.join(CSRC, src), "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"nvcc failed for {name}:\n{r.stderr}")
@@ -77,15 +81,15 @@ def build(force: bool = False, jobs: int | None = None, verbose: bool = False) -
 
     with cf.ThreadPoolExecutor(max_workers=jobs) as pool:
         objs = list(pool.map(compile_unit, UNITS))
-    tmp = LIB_PATH + f".tmp{os.getpid()}"
+    tmp = lib_path + f".tmp{os.getpid()}"
     cmd = [exe, *ARCH, "-shared", "-cudart", "static", "-o", tmp, *objs]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stderr}")
-    os.replace(tmp, LIB_PATH)
+    os.replace(tmp, lib_path)
     with open(stamp, "w") as f:
         f.write(digest)
-    return LIB_PATH
+    return lib_path
 
 
 if __name__ == "__main__":  # pragma: no cover

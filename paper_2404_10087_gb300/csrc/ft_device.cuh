@@ -24,6 +24,16 @@
 #define FT_MAXN 8
 #define FT_TILE 16
 
+// Cache path of the factor-phase row gathers (rows that other warps write
+// during the pass): 0 = L2 only (ld.global.cg), 1 = L1 and L2 (ld.global.ca),
+// 2 = read-only path (ld.global.nc, as the paper's __ldg).  L1 caching keeps
+// the Zipf-hot rows on the SM (L2-only gathers of hot rows were 4x slower on
+// the Netflix-shaped workload); a row another SM wrote meanwhile may be read
+// stale, which the Hogwild pass tolerates as the paper's __ldg reads do.
+#ifndef FT_FACTOR_LOAD
+#define FT_FACTOR_LOAD 1
+#endif
+
 namespace ft {
 
 enum Math { MATH_FP32 = 0, MATH_TF32 = 1, MATH_BF16 = 2 };
@@ -248,7 +258,8 @@ __device__ __forceinline__ void load_chunk(const float *__restrict__ An, int64_t
 #pragma unroll
     for (int w = 0; w < CPL; w += 4) {
       float4 f;
-      if constexpr (READ_ONLY) f = __ldg(reinterpret_cast<const float4 *>(p + w));
+      if constexpr (READ_ONLY || FT_FACTOR_LOAD == 2) f = __ldg(reinterpret_cast<const float4 *>(p + w));
+      else if constexpr (FT_FACTOR_LOAD == 1) f = __ldca(reinterpret_cast<const float4 *>(p + w));
       else f = __ldcg(reinterpret_cast<const float4 *>(p + w));
       v[w] = f.x; v[w + 1] = f.y; v[w + 2] = f.z; v[w + 3] = f.w;
     }
@@ -256,7 +267,8 @@ __device__ __forceinline__ void load_chunk(const float *__restrict__ An, int64_t
 #pragma unroll
     for (int q = 0; q < CPL; ++q) {
       const int j = CPL * t + q;
-      if (j < J) v[q] = READ_ONLY ? __ldg(p + q) : __ldcg(p + q);
+      if (j < J) v[q] = (READ_ONLY || FT_FACTOR_LOAD == 2) ? __ldg(p + q)
+                        : (FT_FACTOR_LOAD == 1 ? __ldca(p + q) : __ldcg(p + q));
       else v[q] = 0.f;
     }
   }

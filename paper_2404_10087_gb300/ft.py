@@ -51,7 +51,8 @@ _P = ctypes.c_void_p
 
 
 def library_path() -> str:
-    return _build.LIB_PATH
+    """The in-tree library, or the file named by FT_LIBRARY (a variant build)."""
+    return os.environ.get("FT_LIBRARY") or _build.LIB_PATH
 
 
 def load(path: str | None = None):
@@ -60,7 +61,7 @@ def load(path: str | None = None):
     with _lock:
         if _lib is not None and path is None:
             return _lib
-        p = path or _build.LIB_PATH
+        p = path or library_path()
         if not os.path.exists(p):
             raise ImportError(f"CUDA library not built: {p} is missing (run __graft_entry__.build())")
         lib = ctypes.CDLL(p)

@@ -82,6 +82,33 @@ def dedup_coords(idx: torch.Tensor) -> torch.Tensor:
     return idx[:, keep_pos]
 
 
+def draw_unique_coords(gen: torch.Generator, I, target: int, dist: str, s: float, device="cpu",
+                       max_rounds: int = 12) -> torch.Tensor:
+    """``target`` distinct coordinates ([N, target] int64, random order).
+
+    Skewed laws repeat popular coordinates, so coordinates are drawn in rounds
+    until ``target`` distinct ones exist; each round's size follows the
+    fraction of new coordinates the previous round produced.  Earlier draws
+    keep their place, so a smaller target is a prefix-like sample of the same
+    recipe."""
+    idx = torch.empty((len(I), 0), dtype=torch.int64, device=device)
+    want = target
+    for _ in range(max_rounds):
+        if want <= 0:
+            break
+        cols = torch.stack([draw_mode_indices(gen, In, want, dist, s, device) for In in I])
+        before = idx.shape[1]
+        idx = dedup_coords(torch.cat([idx, cols], dim=1))
+        gained = idx.shape[1] - before
+        if idx.shape[1] >= target:
+            break
+        frac = max(gained / max(want, 1), 0.02)
+        want = int(min((target - idx.shape[1]) / frac * 1.15 + 1024, 3 * target + 1024))
+    if idx.shape[1] < target:
+        raise RuntimeError(f"could not draw {target} distinct coordinates")
+    return idx[:, :target].contiguous()
+
+
 def normal_matrices(gen: torch.Generator, shapes, std: float, device="cpu",
                     dtype=torch.float32):
     """One N(0, std^2) matrix per shape (std is the standard deviation)."""
@@ -178,10 +205,8 @@ def draw_workload(w: Workload, device="cpu", nnz: int | None = None) -> Draw:
     ``nnz`` overrides the coordinate count (a prefix-sized sample of the
     same recipe)."""
     gen = generator(w.seed, device)
-    n_coords = int(w.nnz if nnz is None else nnz)
-    cols = [draw_mode_indices(gen, I, n_coords, w.dist, w.zipf_s, device) for I in w.I]
-    idx = dedup_coords(torch.stack(cols))
-    del cols
+    target = int(w.nnz if nnz is None else nnz)
+    idx = draw_unique_coords(gen, w.I, target, w.dist, w.zipf_s, device)
     nnz_u = idx.shape[1]
     std_of = (lambda J: w.planted_std) if w.planted_std is not None else (lambda J: 1.0 / math.sqrt(J))
     A = [normal_matrices(gen, [(I, J)], std_of(J), device)[0] for I, J in zip(w.I, w.J)]
@@ -210,15 +235,18 @@ def initial_factors(w: Workload, device="cpu", mean_value: float | None = None, 
     return A, B
 
 
-def random_problem(seed: int, I, J, R, nnz, device="cpu", std=0.5, value_std=1.0):
+def random_problem(seed: int, I, J, R, nnz, device="cpu", std=None, value_std=1.0):
     """A small unstructured problem for parity tests: uniform coordinates
-    (duplicates allowed), N(0, std^2) factors and cores, N(0, value_std^2)
-    values."""
+    (duplicates allowed), N(0, s_n^2) factors and cores, N(0, value_std^2)
+    values.  By default s_n = (R^(-1/N) / J_n)^(1/4), which makes every
+    a^(n) B^(n) entry of variance R^(-1/N) and the prediction of variance
+    about 1, so SGD steps stay well scaled for any N, J, R."""
     gen = generator(seed, device)
     N = len(I)
     idx = torch.stack([torch.randint(0, int(In), (nnz,), generator=gen, device=device)
                        for In in I]).to(torch.int32)
-    A = [normal_matrices(gen, [(In, Jn)], std, device)[0] for In, Jn in zip(I, J)]
-    B = [normal_matrices(gen, [(Jn, R)], std, device)[0] for Jn in J]
+    sd = [std if std is not None else (R ** (-1.0 / N) / Jn) ** 0.25 for Jn in J]
+    A = [normal_matrices(gen, [(In, Jn)], s, device)[0] for In, Jn, s in zip(I, J, sd)]
+    B = [normal_matrices(gen, [(Jn, R)], s, device)[0] for Jn, s in zip(J, sd)]
     x = (torch.randn(nnz, generator=gen, device=device, dtype=torch.float64) * value_std).to(torch.float32)
     return idx, x, A, B

@@ -1,12 +1,16 @@
 """GPU path against the FP64 oracle, through the C ABI.
 
 Tolerances (relative; denominators as stated):
-  * FP32 path: predictions and per-element core gradients <= 1e-5 with the
-    denominator max(|ref|, 1e-3 * RMS(ref)); one deterministic factor
+  * FP32 path: predictions <= 1e-5 relative to the same model evaluated on
+    |A|, |B| (the scale of the FP32 rounding bound, so cancellation does not
+    count against the kernel) and <= 1e-5 in Frobenius norm; core gradients
+    <= 1e-5 elementwise relative to the absolute-value model of the
+    gradient and in Frobenius norm; one deterministic factor
     epoch's factors <= 1e-4 (Frobenius per matrix) and its step
     A_new - A_old <= 1e-4; one core epoch's B <= 1e-5.
-  * TF32 path: steps and gradients <= 5e-3 (Frobenius).
-  * BF16 path: steps and gradients <= 2e-2 (Frobenius).
+  * TF32 path: steps (Frobenius) and gradients (absolute-value model) <= 5e-3.
+  * BF16 path: the same at <= 2e-2; trained test RMSE within 1% of the
+    FP64 oracle's.
 Sizes span several 16-nonzero tiles with a ragged tail.
 """
 import math
@@ -41,6 +45,24 @@ def rel_elem(got, ref):
     return float(np.max(np.abs(got - ref) / den)) if ref.size else 0.0
 
 
+def rel_bound(got, ref, scale):
+    """Forward error relative to the absolute-value model: |got - ref| over
+    the same computation on |A|, |B| (the scale a rounding-error bound of
+    sums of products is proportional to)."""
+    got, ref, scale = (np.asarray(v, np.float64) for v in (got, ref, scale))
+    return float(np.max(np.abs(got - ref) / np.maximum(scale, 1e-300))) if ref.size else 0.0
+
+
+def core_grad_scale(A, B, idx, x):
+    """sum_m |e_m| |a^(n)|^T prod_{k != n} |a^(k)| |B^(k)| - the absolute-value
+    model of the core gradient, obtained from the oracle by evaluating it on
+    |A|, |B| with values shifted so that every residual equals |e_m|."""
+    e = x - oracle.predict(A, B, idx)
+    Aa, Ba = [np.abs(a) for a in A], [np.abs(b) for b in B]
+    shifted = oracle.predict(Aa, Ba, idx) - np.abs(e)
+    return oracle.core_grad(Aa, Ba, idx, shifted)
+
+
 def rel_fro(got, ref):
     got, ref = np.asarray(got, np.float64), np.asarray(ref, np.float64)
     d = np.linalg.norm(ref)
@@ -55,7 +77,7 @@ SHAPES = [
     ((25,), (8,), 5, 77),
     ((20, 21, 22, 23), (32, 32, 32, 32), 32, 16 * 20 + 9),
     ((20, 21, 22, 23, 24), (16, 12, 10, 8, 16), 16, 400),
-    ((9, 10, 11, 12, 13, 14, 15, 16), (4, 4, 4, 4, 4, 4, 4, 4), 4, 300),
+    ((40, 41, 42, 43, 44, 45, 46, 47), (4, 4, 4, 4, 4, 4, 4, 4), 4, 300),
     ((40, 40, 40), (20, 24, 17), 29, 700),
 ]
 SHAPE_IDS = [f"N{len(s[0])}_J{max(s[1])}_R{s[2]}_nnz{s[3]}" for s in SHAPES]
@@ -69,7 +91,9 @@ def test_predict_fp32(shape):
     m = ft.FastTuckerPlus(gidx, gx, gA, gB)
     got = m.predict(gidx).double().cpu().numpy()
     ref = oracle.predict(f64(A), f64(B), idx.numpy())
-    assert rel_elem(got, ref) <= 1e-5
+    scale = oracle.predict([np.abs(a) for a in f64(A)], [np.abs(b) for b in f64(B)], idx.numpy())
+    assert rel_bound(got, ref, scale) <= 1e-5
+    assert rel_fro(got, ref) <= 1e-5
 
 
 @pytest.mark.parametrize("precision", ["fp32", "tf32", "bf16"])
@@ -100,11 +124,13 @@ def test_core_gradient(shape, precision):
     gidx, gx, gA, gB = to_dev(idx, x, A, B)
     m = ft.FastTuckerPlus(gidx, gx, gA, gB, precision=precision)
     G = f64(m.core_grad())
-    ref = oracle.core_grad(f64(A), f64(B), idx.numpy(), x.double().numpy())
+    A64, B64, i64, x64 = f64(A), f64(B), idx.numpy(), x.double().numpy()
+    ref = oracle.core_grad(A64, B64, i64, x64)
+    scale = core_grad_scale(A64, B64, i64, x64)
     for n in range(len(I)):
+        assert rel_bound(G[n], ref[n], scale[n]) <= TOL_GRAD[precision], n
         if precision == "fp32":
-            assert rel_elem(G[n], ref[n]) <= 1e-5, n
-        assert rel_fro(G[n], ref[n]) <= TOL_GRAD[precision], n
+            assert rel_fro(G[n], ref[n]) <= 1e-5, n
 
 
 @pytest.mark.parametrize("precision", ["fp32", "bf16"])
@@ -175,25 +201,62 @@ def test_deterministic_mode_is_bitwise_reproducible():
         assert torch.equal(a, b)
 
 
-def test_planted_training_tracks_oracle():
-    """Ten epochs on the planted 3-order workload (1e5 uniform coordinates,
-    planted J = R = 4 with noise 0.1): the Hogwild FP32 run and the sequential
-    oracle reach test RMSE within 2% of each other."""
+def planted_setup():
     w = synth.WORKLOADS["planted_uniform_1e5"]
     d = synth.draw_workload(w)
     planted = oracle.predict(f64(d.planted_A), f64(d.planted_B), d.idx.numpy())
     x = (torch.from_numpy(planted) + d.noise.double()).float()
-    tr, te = d.train, d.test
     A0, B0 = synth.initial_factors(w)
+    return w, d, x, A0, B0
+
+
+@pytest.mark.parametrize("precision,tol", [("fp32", 1e-4), ("tf32", 1e-2), ("bf16", 1e-2)])
+def test_planted_training_matches_oracle(precision, tol):
+    """Ten deterministic epochs (batch 256) on the planted 3-order workload
+    (1e5 uniform coordinates, planted J = R = 4, noise 0.1): test RMSE of the
+    GPU run within `tol` (relative) of the FP64 oracle's run."""
+    w, d, x, A0, B0 = planted_setup()
+    tr, te = d.train, d.test
     gA = [a.clone().to(DEV) for a in A0]
     gB = [b.clone().to(DEV) for b in B0]
     tri = [d.idx[n, tr].contiguous().to(DEV) for n in range(3)]
     tei = [d.idx[n, te].contiguous().to(DEV) for n in range(3)]
-    m = ft.FastTuckerPlus(tri, x[tr].contiguous().to(DEV), gA, gB)
+    S = 256
+    m = ft.FastTuckerPlus(tri, x[tr].contiguous().to(DEV), gA, gB, precision=precision,
+                          scatter="deterministic", det_batch=S)
     lr = lam = 0.01
     oA, oB = f64(A0), f64(B0)
     itr, ite = d.idx[:, tr].numpy(), d.idx[:, te].numpy()
     xtr, xte = x[tr].double().numpy(), x[te].double().numpy()
+    r0 = oracle.errors(oA, oB, ite, xte)[0]
+    for _ in range(10):
+        m.epoch_factors(lr, lam)
+        m.epoch_core(lr, lam)
+        oA = oracle.factor_epoch(oA, oB, itr, xtr, S, lr, lam)
+        oB = oracle.core_epoch(oA, oB, itr, xtr, lr, lam, nthreads=oracle.default_threads())
+    g = m.rmse(tei, x[te].contiguous().to(DEV))[0]
+    o = oracle.errors(oA, oB, ite, xte)[0]
+    assert o < 0.5 * r0
+    assert abs(g - o) <= tol * o, (g, o)
+
+
+@pytest.mark.parametrize("precision", ["fp32", "bf16"])
+def test_hogwild_training_converges(precision):
+    """The Hogwild pass (concurrent row updates may be lost) still trains:
+    ten epochs reach a test RMSE within 35% of the sequential FP64 oracle's
+    and far below the starting error."""
+    w, d, x, A0, B0 = planted_setup()
+    tr, te = d.train, d.test
+    gA = [a.clone().to(DEV) for a in A0]
+    gB = [b.clone().to(DEV) for b in B0]
+    tri = [d.idx[n, tr].contiguous().to(DEV) for n in range(3)]
+    tei = [d.idx[n, te].contiguous().to(DEV) for n in range(3)]
+    m = ft.FastTuckerPlus(tri, x[tr].contiguous().to(DEV), gA, gB, precision=precision)
+    lr = lam = 0.01
+    oA, oB = f64(A0), f64(B0)
+    itr, ite = d.idx[:, tr].numpy(), d.idx[:, te].numpy()
+    xtr, xte = x[tr].double().numpy(), x[te].double().numpy()
+    r0 = oracle.errors(oA, oB, ite, xte)[0]
     for _ in range(10):
         m.epoch_factors(lr, lam)
         m.epoch_core(lr, lam)
@@ -201,7 +264,8 @@ def test_planted_training_tracks_oracle():
         oB = oracle.core_epoch(oA, oB, itr, xtr, lr, lam, nthreads=oracle.default_threads())
     g = m.rmse(tei, x[te].contiguous().to(DEV))[0]
     o = oracle.errors(oA, oB, ite, xte)[0]
-    assert abs(g - o) <= 0.02 * o, (g, o)
+    assert g < 0.6 * r0, (g, r0)
+    assert g <= 1.35 * o, (g, o)
 
 
 # ------------------------------------------------------------ edge cases
