@@ -136,10 +136,11 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def make_workload(device, nnz=None):
+def make_workload(device, nnz=None, name=WORKLOAD):
     """Draw the synthetic tensor on `device`; planted values are computed by the
-    library's own predict call, then mapped to integer ratings 1..5."""
-    w = synth.WORKLOADS[WORKLOAD]
+    library's own predict call, then mapped to integer ratings 1..5 (ratings
+    workloads) or given the workload's noise."""
+    w = synth.WORKLOADS[name]
     d = synth.draw_workload(w, device=device, nnz=nnz)
     N = w.N
     allidx = [d.idx[n].contiguous() for n in range(N)]
@@ -149,7 +150,7 @@ def make_workload(device, nnz=None):
     pred = pm.predict(allidx)
     pm.close()
     del zeros
-    vals = synth.to_ratings(pred)
+    vals = synth.to_ratings(pred) if w.ratings else pred + d.noise
     del pred
     tr, te = d.train, d.test
     train_idx = [d.idx[n, tr].contiguous() for n in range(N)]
@@ -164,11 +165,12 @@ def run_ours(args, rank, world, local_rank):
     dev = torch.device(f"cuda:{local_rank}")
     torch.cuda.set_device(dev)
     ft.load()
-    w, tri, trx, tei, tex, A, B = make_workload(dev, args.nnz)
+    w, tri, trx, tei, tex, A, B = make_workload(dev, args.nnz, args.workload)
     N, J, R = w.N, list(w.J), w.R
     nnz_train, nnz_test = int(trx.numel()), int(tex.numel())
     stream = torch.cuda.current_stream(dev)
-    m = ft.FastTuckerPlus(tri, trx, A, B, precision=args.precision, scatter="hogwild")
+    m = ft.FastTuckerPlus(tri, trx, A, B, precision=args.precision, scatter="hogwild",
+                          hot_rows=args.hot_rows, hot_window=args.hot_window)
 
     ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
 
@@ -259,9 +261,10 @@ def run_ours(args, rank, world, local_rank):
         "dtype": {"fp32": "f32", "tf32": "tf32", "bf16": "bf16"}[args.precision],
         "data": "synthetic (seeded Zipf coordinates, planted-model ratings; Netflix-shaped)",
         "config": {
-            "workload": WORKLOAD if args.nnz is None else f"{WORKLOAD} at {args.nnz} coordinates", "N": N, "I": list(w.I), "J": J, "R": R,
+            "workload": args.workload if args.nnz is None else f"{args.workload} at {args.nnz} coordinates", "N": N, "I": list(w.I), "J": J, "R": R,
             "nnz_train": nnz_train, "nnz_test": nnz_test, "precision": args.precision,
-            "scatter": "hogwild", "lr": LR, "lambda": LAM,
+            "scatter": "hogwild", "hot_rows": m.cfg.hot_rows, "hot_window": m.cfg.hot_window,
+            "lr": LR, "lambda": LAM,
             "parallelism": "replicas" if world > 1 else "single",
             "l2": "inputs larger than L2 (training COO stream 1.2 GB per epoch)",
         },
@@ -357,6 +360,11 @@ def main():
     ap.add_argument("--cpu-sample", type=int, default=2_000_000)
     ap.add_argument("--ref-sample", type=int, default=1_000_000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--hot-rows", type=int, default=None,
+                    help="rows per mode in the shared-memory hot-row cache (-1 auto, 0 off)")
+    ap.add_argument("--hot-window", type=int, default=None, help="CTA tiles between cache write-backs")
+    ap.add_argument("--workload", default=WORKLOAD, choices=sorted(synth.WORKLOADS),
+                    help="the timed tensor (default: the Netflix-shaped 1e8 Zipf tensor)")
     ap.add_argument("--nnz", type=int, default=None,
                     help="distinct coordinates drawn (default: the workload's 1e8); "
                          "a smaller case of the same recipe, e.g. for profiling")

@@ -39,10 +39,10 @@ def nvcc() -> str:
     return cand
 
 
-def _sources_digest(extra=()) -> str:
+def _sources_digest(extra=(), csrc=CSRC) -> str:
     h = hashlib.sha256()
-    for name in sorted(os.listdir(CSRC)):
-        with open(os.path.join(CSRC, name), "rb") as f:
+    for name in sorted(os.listdir(csrc)):
+        with open(os.path.join(csrc, name), "rb") as f:
             h.update(name.encode())
             h.update(f.read())
     with open(os.path.join(INCLUDE, "ft.h"), "rb") as f:
@@ -52,15 +52,16 @@ def _sources_digest(extra=()) -> str:
 
 
 def build(force: bool = False, jobs: int | None = None, verbose: bool = False,
-          extra_defines=(), out_dir: str | None = None) -> str:
+          extra_defines=(), out_dir: str | None = None, csrc: str = CSRC) -> str:
     """Compile every unit (in parallel) and link ``libft.so``; skipped when the
     sources are unchanged since the last build.  ``extra_defines`` and
-    ``out_dir`` build a variant elsewhere (e.g. another cache policy)."""
+    ``out_dir`` build a variant elsewhere (e.g. another cache policy);
+    ``csrc`` compiles another source tree with the same flags."""
     out_dir = out_dir or OUT_DIR
     lib_path = os.path.join(out_dir, "libft.so")
     os.makedirs(out_dir, exist_ok=True)
     stamp = os.path.join(out_dir, "sources.sha256")
-    digest = _sources_digest(extra_defines)
+    digest = _sources_digest(extra_defines, csrc)
     if not force and os.path.exists(lib_path) and os.path.exists(stamp):
         with open(stamp) as f:
             if f.read().strip() == digest:
@@ -71,7 +72,8 @@ def build(force: bool = False, jobs: int | None = None, verbose: bool = False,
     def compile_unit(unit):
         src, defs, name = unit
         obj = os.path.join(out_dir, name + ".o")
-        cmd = [exe, *ARCH, *NVCC_FLAGS, *extra_defines, *defs, "-c", os.path.join(CSRC, src), "-o", obj]
+        flags = [f if f != f"-I{CSRC}" else f"-I{csrc}" for f in NVCC_FLAGS]
+        cmd = [exe, *ARCH, *flags, *extra_defines, *defs, "-c", os.path.join(csrc, src), "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"nvcc failed for {name}:\n{r.stderr}")

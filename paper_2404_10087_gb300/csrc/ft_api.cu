@@ -136,6 +136,39 @@ __global__ void k_errors_final(const ErrFinalArgs a) {
   a.out3[2] = se;
 }
 
+struct CountArgs {
+  const int32_t *idx[FT_MAXN];
+  int32_t *counts[FT_MAXN];
+  int N;
+  int64_t nnz;
+};
+
+// Training nonzeros per row of every mode (selects the cached hot rows).
+__global__ void k_row_counts(const CountArgs a) {
+  for (int64_t m = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; m < a.nnz;
+       m += int64_t(gridDim.x) * blockDim.x)
+    for (int n = 0; n < a.N; ++n) atomicAdd(a.counts[n] + a.idx[n][m], 1);
+}
+
+struct RemapArgs {
+  const int32_t *idx[FT_MAXN];
+  int32_t *out[FT_MAXN];
+  const int32_t *slot_of[FT_MAXN];
+  int N;
+  int64_t nnz;
+};
+
+// Coordinates of the Hogwild pass: a cached row becomes -(slot + 1).
+__global__ void k_remap(const RemapArgs a) {
+  for (int64_t m = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; m < a.nnz;
+       m += int64_t(gridDim.x) * blockDim.x)
+    for (int n = 0; n < a.N; ++n) {
+      const int32_t v = a.idx[n][m];
+      const int32_t sl = a.slot_of[n][v];
+      a.out[n][m] = sl >= 0 ? -(sl + 1) : v;
+    }
+}
+
 // ------------------------------------------------------------------- plan
 struct Plan {
   int N = 0, R = 0, K = 0, sumJ = 0;
@@ -149,10 +182,16 @@ struct Plan {
   ft::EvalSet es;
   int grid_factor = 0, grid_core = 0, grid_eval = 0;
   int64_t det_S = 0, nbatches = 0;
+  int hot_cap = 0;                   // cache slots per mode (0 = no cache)
+  size_t factor_smem = 0;            // Hogwild pass, tables + cache
   // workspace offsets
   size_t off_err = 0, off_out = 0, off_partial = 0, off_errpart = 0, off_delta = 0;
-  size_t off_order = 0, off_segptr = 0, off_segrow = 0, total = 0;
+  size_t off_order = 0, off_segptr = 0, off_segrow = 0;
+  size_t off_remap = 0, off_hot = 0, off_counts = 0, total = 0;
 };
+
+constexpr size_t kHotCacheBytes = 64 * 1024;
+constexpr size_t kMaxSmem = 227 * 1024;
 
 ft_status cuda_status(cudaError_t e) { return e == cudaSuccess ? FT_OK : FT_ERR_CUDA; }
 
@@ -177,6 +216,9 @@ ft_status make_plan(int N, const int64_t *I, const int *J, int R, int64_t nnz, c
   if (c.scatter != FT_HOGWILD && c.scatter != FT_DETERMINISTIC) return FT_ERR_ARG;
   if (c.scatter == FT_DETERMINISTIC && c.det_batch < 1) return FT_ERR_ARG;
   if (c.blocks_per_sm < 0) return FT_ERR_ARG;
+  if (c.hot_rows < -1 || c.hot_window < 1 || c.hot_min_count < 1) return FT_ERR_ARG;
+  for (int q = 0; q < 4; ++q)
+    if (c.reserved[q] != 0) return FT_ERR_ARG;
   int maxr = R;
   p->sumJ = 0;
   for (int n = 0; n < N; ++n) {
@@ -211,7 +253,20 @@ ft_status make_plan(int N, const int64_t *I, const int *J, int R, int64_t nnz, c
   if (cudaGetDevice(&p->dev) != cudaSuccess) return FT_ERR_CUDA;
   if (cudaDeviceGetAttribute(&p->num_sms, cudaDevAttrMultiProcessorCount, p->dev) != cudaSuccess)
     return FT_ERR_CUDA;
-  const int occ_f = occupancy(p->ks.factor, 256, p->ks.factor_smem);
+  int64_t maxI = 1;
+  for (int n = 0; n < N; ++n) maxI = std::max(maxI, I[n]);
+  p->hot_cap = 0;
+  if (c.scatter == FT_HOGWILD && c.hot_rows != 0 && nnz > 0) {
+    int64_t cap = c.hot_rows > 0 ? c.hot_rows : int64_t(kHotCacheBytes / (size_t(N) * K * sizeof(float)));
+    cap = std::min(cap, maxI);
+    const size_t per_slot = size_t(N) * K * sizeof(float) + N;
+    const int64_t fit = int64_t((kMaxSmem - p->ks.factor_smem - 64) / per_slot);
+    if (cap > fit) return FT_ERR_ARG;
+    p->hot_cap = int(std::max<int64_t>(cap, 0));
+  }
+  p->factor_smem = p->ks.factor_smem + size_t(N) * p->hot_cap * K * sizeof(float) +
+                   ((size_t(N) * p->hot_cap + 15) / 16) * 16;
+  const int occ_f = occupancy(p->ks.factor, 256, p->factor_smem);
   const int occ_d = occupancy(p->ks.factor_delta, 256, p->ks.factor_smem);
   const int occ_c = occupancy(p->ks.core, p->ks.core_threads, p->ks.core_smem);
   const int occ_p = occupancy(p->es.predict, 256, p->es.smem);
@@ -227,6 +282,13 @@ ft_status make_plan(int N, const int64_t *I, const int *J, int R, int64_t nnz, c
   p->off_out = off;     off += align_up(sizeof(double) * 4);
   p->off_partial = off; off += align_up(sizeof(float) * 2 * size_t(p->grid_core) * N * K * K);
   p->off_errpart = off; off += align_up(sizeof(double) * 2 * size_t(p->grid_eval));
+  if (p->hot_cap > 0) {
+    int64_t sumI = 0;
+    for (int n = 0; n < N; ++n) sumI += I[n];
+    p->off_remap = off;  off += align_up(sizeof(int32_t) * size_t(N) * nnz);
+    p->off_hot = off;    off += align_up(sizeof(int32_t) * size_t(N) * p->hot_cap);
+    p->off_counts = off; off += align_up(sizeof(int32_t) * size_t(sumI));
+  }
   if (c.scatter == FT_DETERMINISTIC) {
     p->det_S = std::max<int64_t>(1, std::min<int64_t>(c.det_batch, std::max<int64_t>(nnz, 1)));
     p->nbatches = nnz > 0 ? (nnz + p->det_S - 1) / p->det_S : 0;
@@ -251,6 +313,8 @@ struct ft_ctx {
   char *ws = nullptr;
   unsigned vecmask = 0;
   std::vector<int64_t> seg_lo[FT_MAXN];  // per mode: first segment of each batch (+ end)
+  int hot_count[FT_MAXN] = {0};          // cached rows per mode (Hogwild)
+  bool hot_active = false;
   int64_t launches = 0;
 };
 
@@ -345,6 +409,78 @@ ft_status build_segments(ft_ctx *c, cudaStream_t st) {
   return FT_OK;
 }
 
+// Hot-row cache of the Hogwild pass: count the nonzeros of every row, keep
+// the hot_cap most frequent rows of each mode that have at least
+// hot_min_count of them, and write the remapped coordinates.
+ft_status build_hot_cache(ft_ctx *c, cudaStream_t st) {
+  const Plan &p = c->p;
+  int64_t sumI = 0;
+  for (int n = 0; n < p.N; ++n) sumI += p.I[n];
+  int32_t *d_counts = ws_ptr<int32_t>(c, p.off_counts);
+  if (cudaMemsetAsync(d_counts, 0, sizeof(int32_t) * sumI, st) != cudaSuccess) return FT_ERR_CUDA;
+  CountArgs ca;
+  memset(&ca, 0, sizeof(ca));
+  int64_t off = 0;
+  for (int n = 0; n < p.N; ++n) {
+    ca.idx[n] = c->idx[n];
+    ca.counts[n] = d_counts + off;
+    off += p.I[n];
+  }
+  ca.N = p.N;
+  ca.nnz = p.nnz;
+  const int grid = int(std::min<int64_t>((p.nnz + 255) / 256, int64_t(p.num_sms) * 8));
+  ft_status s = launch(c, reinterpret_cast<const void *>(&k_row_counts), grid, 256, 0, &ca, st);
+  if (s != FT_OK) return s;
+  std::vector<int32_t> counts(static_cast<size_t>(sumI));
+  if (cudaMemcpyAsync(counts.data(), d_counts, sizeof(int32_t) * sumI, cudaMemcpyDeviceToHost, st) !=
+          cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess)
+    return FT_ERR_CUDA;
+  std::vector<int32_t> slot_of(size_t(sumI), -1);
+  std::vector<int32_t> hot(size_t(p.N) * p.hot_cap, 0);
+  bool any = false;
+  off = 0;
+  for (int n = 0; n < p.N; ++n) {
+    std::vector<int32_t> cand;
+    for (int64_t r = 0; r < p.I[n]; ++r)
+      if (counts[size_t(off + r)] >= p.cfg.hot_min_count) cand.push_back(int32_t(r));
+    const size_t k = std::min(cand.size(), size_t(p.hot_cap));
+    std::partial_sort(cand.begin(), cand.begin() + k, cand.end(), [&](int32_t a, int32_t b) {
+      const int32_t ca_ = counts[size_t(off + a)], cb = counts[size_t(off + b)];
+      return ca_ != cb ? ca_ > cb : a < b;
+    });
+    for (size_t q = 0; q < k; ++q) {
+      hot[size_t(n) * p.hot_cap + q] = cand[q];
+      slot_of[size_t(off + cand[q])] = int32_t(q);
+    }
+    c->hot_count[n] = int(k);
+    any = any || k > 0;
+    off += p.I[n];
+  }
+  c->hot_active = any;
+  if (!any) return FT_OK;
+  int32_t *d_hot = ws_ptr<int32_t>(c, p.off_hot);
+  if (cudaMemcpyAsync(d_hot, hot.data(), sizeof(int32_t) * hot.size(), cudaMemcpyHostToDevice, st) !=
+          cudaSuccess ||
+      cudaMemcpyAsync(d_counts, slot_of.data(), sizeof(int32_t) * sumI, cudaMemcpyHostToDevice, st) !=
+          cudaSuccess)
+    return FT_ERR_CUDA;
+  RemapArgs ra;
+  memset(&ra, 0, sizeof(ra));
+  off = 0;
+  for (int n = 0; n < p.N; ++n) {
+    ra.idx[n] = c->idx[n];
+    ra.out[n] = ws_ptr<int32_t>(c, p.off_remap) + size_t(n) * p.nnz;
+    ra.slot_of[n] = d_counts + off;
+    off += p.I[n];
+  }
+  ra.N = p.N;
+  ra.nnz = p.nnz;
+  s = launch(c, reinterpret_cast<const void *>(&k_remap), grid, 256, 0, &ra, st);
+  if (s != FT_OK) return s;
+  return cudaStreamSynchronize(st) == cudaSuccess ? FT_OK : FT_ERR_CUDA;
+}
+
 ft_status take_error(ft_ctx *c, cudaStream_t st) {
   int err = 0;
   int *d = ws_ptr<int>(c, c->p.off_err);
@@ -368,6 +504,9 @@ void ft_config_default(ft_config *cfg) {
   cfg->scatter = FT_HOGWILD;
   cfg->det_batch = 4096;
   cfg->blocks_per_sm = 0;
+  cfg->hot_rows = -1;
+  cfg->hot_window = 16;
+  cfg->hot_min_count = 2;
 }
 
 ft_status ft_workspace_size(int N, const int64_t *I, const int *J, int R, int64_t nnz,
@@ -429,6 +568,10 @@ ft_status ft_init(ft_ctx **out, int N, const int64_t *I, const int *J, int R, in
     s = build_segments(c, st);
     if (s != FT_OK) { delete c; return s; }
   }
+  if (c->p.hot_cap > 0) {
+    s = build_hot_cache(c, st);
+    if (s != FT_OK) { delete c; return s; }
+  }
   if (cudaStreamSynchronize(st) != cudaSuccess) { delete c; return FT_ERR_CUDA; }
   *out = c;
   return FT_OK;
@@ -446,8 +589,19 @@ ft_status ft_epoch_factors(ft_ctx *c, float lr_a, float lambda_a, const float *c
   a.lam = lambda_a;
   if (row_step_scale)
     for (int n = 0; n < p.N; ++n) a.scale[n] = row_step_scale[n];
-  if (p.cfg.scatter == FT_HOGWILD)
-    return launch(c, p.ks.factor, p.grid_factor, 256, p.ks.factor_smem, &a, st);
+  if (p.cfg.scatter == FT_HOGWILD) {
+    if (c->hot_active) {
+      for (int n = 0; n < p.N; ++n) {
+        a.idx[n] = ws_ptr<int32_t>(c, p.off_remap) + size_t(n) * p.nnz;
+        a.hot_rows[n] = ws_ptr<int32_t>(c, p.off_hot) + size_t(n) * p.hot_cap;
+        a.hot_count[n] = c->hot_count[n];
+      }
+      a.hot_cap = p.hot_cap;
+      a.hot_window = p.cfg.hot_window;
+    }
+    return launch(c, p.ks.factor, p.grid_factor, 256, c->hot_active ? p.factor_smem : p.ks.factor_smem,
+                  &a, st);
+  }
 
   a.delta = ws_ptr<float>(c, p.off_delta);
   ApplyArgs ap;

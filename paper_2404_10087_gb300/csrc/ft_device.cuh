@@ -63,6 +63,12 @@ struct EpochArgs {
   float *pred;                      // predict: outputs (index m - begin)
   double *err_partial;              // errors: per-CTA (sum e^2, sum |e|)
   int *err;                         // latched error word
+  // Hot-row cache of the Hogwild factor pass (see k_factor): idx[n][m] < 0
+  // addresses slot -idx - 1 of mode n, whose global row is hot_rows[n][slot].
+  const int32_t *hot_rows[FT_MAXN];
+  int hot_count[FT_MAXN];           // slots in use per mode
+  int hot_cap;                      // slots per mode in shared memory (0 = no cache)
+  int hot_window;                   // CTA tiles between write-back/refresh
 };
 
 // ------------------------------------------------------------- small helpers
@@ -297,34 +303,49 @@ struct Front {
   static constexpr int CPL = K / 4;
   int64_t m[2];
   bool valid[2];
-  int32_t row[N][2];
+  int32_t row[N][2];                // global row, or cache slot when hot
+  unsigned hot;                     // bit 2n + h: row[n][h] is a cache slot
   float x[2];
   float a[N][2][CPL];
   float c[N][2][CPL];
   float xhat[2];
 
-  __device__ __forceinline__ void load(const EpochArgs &p, int64_t tile_base, int lane, bool need_x) {
+  // rep: the CTA's hot-row cache ([N][hot_cap][K] floats) or null.
+  __device__ __forceinline__ void load(const EpochArgs &p, int64_t tile_base, int lane, bool need_x,
+                                       const float *rep = nullptr) {
     const int g = lane >> 2, t = lane & 3;
     m[0] = tile_base + g;
     m[1] = tile_base + g + 8;
     valid[0] = m[0] < p.end;
     valid[1] = m[1] < p.end;
+    hot = 0u;
 #pragma unroll
     for (int n = 0; n < N; ++n)
 #pragma unroll
       for (int h = 0; h < 2; ++h) row[n][h] = valid[h] ? __ldcs(p.idx[n] + m[h]) : 0;
-    // a coordinate outside [0, I_n) masks its nonzero and latches an error
+    // a coordinate outside [0, I_n) (or a slot outside the cache) masks its
+    // nonzero and latches an error
     bool bad = false;
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
       bool ok = true;
 #pragma unroll
-      for (int n = 0; n < N; ++n) ok = ok && row[n][h] >= 0 && int64_t(row[n][h]) < p.I[n];
+      for (int n = 0; n < N; ++n) {
+        const int32_t v = row[n][h];
+        if (rep != nullptr && v < 0) {
+          ok = ok && (-v - 1) < p.hot_count[n];
+          row[n][h] = -v - 1;
+          hot |= 1u << (2 * n + h);
+        } else {
+          ok = ok && v >= 0 && int64_t(v) < p.I[n];
+        }
+      }
       if (valid[h] && !ok) {
         bad = true;
         valid[h] = false;
 #pragma unroll
         for (int n = 0; n < N; ++n) row[n][h] = 0;
+        hot &= ~((0x55555555u) << h);
       }
     }
     if (bad) atomicOr(p.err, ERRBIT_INDEX);
@@ -333,8 +354,18 @@ struct Front {
 #pragma unroll
     for (int n = 0; n < N; ++n)
 #pragma unroll
-      for (int h = 0; h < 2; ++h)
-        load_chunk<K, READ_ONLY>(p.A[n], row[n][h], p.J[n], t, valid[h], (p.vecmask >> n) & 1, a[n][h]);
+      for (int h = 0; h < 2; ++h) {
+        if ((hot >> (2 * n + h)) & 1u) {
+          const float *src = rep + (size_t(n) * p.hot_cap + row[n][h]) * K + CPL * t;
+#pragma unroll
+          for (int w = 0; w < CPL; w += 4) {
+            const float4 f4 = *reinterpret_cast<const float4 *>(src + w);
+            a[n][h][w] = f4.x; a[n][h][w + 1] = f4.y; a[n][h][w + 2] = f4.z; a[n][h][w + 3] = f4.w;
+          }
+        } else {
+          load_chunk<K, READ_ONLY>(p.A[n], row[n][h], p.J[n], t, valid[h], (p.vecmask >> n) & 1, a[n][h]);
+        }
+      }
   }
 
   __device__ __forceinline__ void compute(const float *tabB, int tab_words, int lane) {
@@ -373,12 +404,16 @@ struct Front {
   }
 };
 
-// Shared-memory table layout of the factor kernel: for each mode, the a.B
-// table, then for each mode the d.B^T table.
+// Shared-memory layout of the factor kernel: for each mode the a.B table,
+// then for each mode the d.B^T table, then (Hogwild pass) the hot-row cache
+// [N][hot_cap][K] floats and its dirty flags [N][hot_cap] bytes.
 template <int N, int K, int MATH>
 struct FactorSmem {
   static constexpr int TW = Prod<K, MATH>::WORDS;
-  static constexpr size_t bytes() { return size_t(2) * N * TW * sizeof(float); }
+  static constexpr size_t tables() { return size_t(2) * N * TW * sizeof(float); }
+  static constexpr size_t bytes(int hot_cap) {
+    return tables() + size_t(N) * hot_cap * K * sizeof(float) + ((size_t(N) * hot_cap + 15) / 16) * 16;
+  }
 };
 
 template <int N, int K, int MATH>
@@ -391,60 +426,168 @@ __device__ __forceinline__ void fill_tables(float *smem, const EpochArgs &p, boo
   }
 }
 
-// ------------------------------------------------------------- factor phase
-// One pass of the factor update over [begin, end) (Algorithm 4):
-//   C = A_Psi B, D = *_{k != n} C, P = D B^T, e = x - xhat,
+// Hot-row cache traffic (whole CTA): refresh every slot from L2, or write the
+// dirty slots back and clear their flags.
+template <int N, int K>
+__device__ void cache_refresh(const EpochArgs &p, float *rep) {
+  for (int e = threadIdx.x; e < N * p.hot_cap * (K / 4); e += blockDim.x) {
+    const int n = e / (p.hot_cap * (K / 4));
+    const int rem = e % (p.hot_cap * (K / 4));
+    const int slot = rem / (K / 4), j0 = 4 * (rem % (K / 4));
+    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (slot < p.hot_count[n] && j0 < p.J[n]) {
+      const float *src = p.A[n] + int64_t(__ldg(p.hot_rows[n] + slot)) * p.J[n] + j0;
+      if (((p.vecmask >> n) & 1) != 0) {
+        v = __ldcg(reinterpret_cast<const float4 *>(src));
+      } else {
+        v.x = __ldcg(src);
+        if (j0 + 1 < p.J[n]) v.y = __ldcg(src + 1);
+        if (j0 + 2 < p.J[n]) v.z = __ldcg(src + 2);
+        if (j0 + 3 < p.J[n]) v.w = __ldcg(src + 3);
+      }
+    }
+    *reinterpret_cast<float4 *>(rep + (size_t(n) * p.hot_cap + slot) * K + j0) = v;
+  }
+}
+
+template <int N, int K>
+__device__ void cache_write_back(const EpochArgs &p, const float *rep, unsigned char *dirty) {
+  for (int e = threadIdx.x; e < N * p.hot_cap * (K / 4); e += blockDim.x) {
+    const int n = e / (p.hot_cap * (K / 4));
+    const int rem = e % (p.hot_cap * (K / 4));
+    const int slot = rem / (K / 4), j0 = 4 * (rem % (K / 4));
+    if (slot >= p.hot_count[n] || j0 >= p.J[n] || !dirty[n * p.hot_cap + slot]) continue;
+    const float4 v = *reinterpret_cast<const float4 *>(rep + (size_t(n) * p.hot_cap + slot) * K + j0);
+    float *dst = p.A[n] + int64_t(__ldg(p.hot_rows[n] + slot)) * p.J[n] + j0;
+    if (((p.vecmask >> n) & 1) != 0) {
+      __stcg(reinterpret_cast<float4 *>(dst), v);
+    } else {
+      __stcg(dst, v.x);
+      if (j0 + 1 < p.J[n]) __stcg(dst + 1, v.y);
+      if (j0 + 2 < p.J[n]) __stcg(dst + 2, v.z);
+      if (j0 + 3 < p.J[n]) __stcg(dst + 3, v.w);
+    }
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < N * p.hot_cap; e += blockDim.x) dirty[e] = 0;
+}
+
+// One factor-phase tile (Algorithm 4): C = A_Psi B, D = *_{k != n} C,
+// P = D B^T, e = x - xhat, then per mode either the new rows
 //   a <- a + lr * s_row * (e P - lam a)   (Eq. "Update_FastTuckerPlus_factor")
-// DELTA = false: rows are stored back at once (Hogwild, as in the paper).
-// DELTA = true: the per-nonzero step e P - lam a is written to p.delta for the
+// are stored (Hogwild; hot rows go to the CTA's cache), or (DELTA) the
+// per-nonzero step e P - lam a is written for the deterministic reduction.
+template <int N, int K, int MATH, bool DELTA>
+__device__ __forceinline__ void factor_tile(const EpochArgs &p, const float *tabs, float *rep,
+                                            unsigned char *dirty, int64_t tile, int lane) {
+  constexpr int CPL = K / 4;
+  constexpr int TW = Prod<K, MATH>::WORDS;
+  const int t = lane & 3;
+  Front<N, K, MATH, false> f;
+  f.load(p, p.begin + tile * FT_TILE, lane, true, rep);
+  f.compute(tabs, TW, lane);
+  float e[2];
+  e[0] = f.x[0] - f.xhat[0];
+  e[1] = f.x[1] - f.xhat[1];
+  const bool bad = (f.valid[0] && !isfinite(e[0])) || (f.valid[1] && !isfinite(e[1]));
+  if (__any_sync(FULL, bad) && lane == 0) atomicOr(p.err, ERRBIT_NONFINITE);
+#pragma unroll
+  for (int n = 0; n < N; ++n) {
+    float d[2][CPL], pp[2][CPL];
+    f.leave_one_out(n, d);
+    Prod<K, MATH>::run(d, tabs + (N + n) * TW, pp, lane);
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      if (!f.valid[h]) continue;
+      float out[CPL];
+      if constexpr (DELTA) {
+#pragma unroll
+        for (int q = 0; q < CPL; ++q) out[q] = e[h] * pp[h][q] - p.lam * f.a[n][h][q];
+        float *dst = p.delta + (f.m[h] - p.begin) * p.sumJ + p.offJ[n] + CPL * t;
+#pragma unroll
+        for (int q = 0; q < CPL; ++q)
+          if (CPL * t + q < p.J[n]) dst[q] = out[q];
+      } else {
+        const bool is_hot = (f.hot >> (2 * n + h)) & 1u;
+        float lr = p.lr;
+        if (p.scale[n]) {
+          const int64_t grow = is_hot ? int64_t(__ldg(p.hot_rows[n] + f.row[n][h])) : int64_t(f.row[n][h]);
+          lr *= __ldg(p.scale[n] + grow);
+        }
+#pragma unroll
+        for (int q = 0; q < CPL; ++q)
+          out[q] = fmaf(lr, fmaf(e[h], pp[h][q], -p.lam * f.a[n][h][q]), f.a[n][h][q]);
+        if (is_hot) {
+          float *dst = rep + (size_t(n) * p.hot_cap + f.row[n][h]) * K + CPL * t;
+#pragma unroll
+          for (int w = 0; w < CPL; w += 4)
+            *reinterpret_cast<float4 *>(dst + w) = make_float4(out[w], out[w + 1], out[w + 2], out[w + 3]);
+          if (t == 0) dirty[n * p.hot_cap + f.row[n][h]] = 1;
+        } else {
+          store_chunk<K>(p.A[n], f.row[n][h], p.J[n], t, (p.vecmask >> n) & 1, out);
+        }
+      }
+    }
+  }
+}
+
+// ------------------------------------------------------------- factor phase
+// One pass of the factor update over [begin, end) (Algorithm 4).
+//
+// DELTA = false (Hogwild, as the paper's kernel): rows are stored back as soon
+// as a tile is done.  Rows that many nonzeros share are the costly ones on
+// GB300 - every store to a line that other SMs keep reading turns their
+// next reads into slow coherence misses, and the stores themselves queue on
+// the hottest lines.  So the hottest rows of every mode (chosen at ft_init
+// from the row counts) live in a per-CTA write-back cache in shared memory:
+// the CTA's warps read and update the cached copy, and every hot_window CTA
+// tiles the CTA writes its dirty rows back to global memory (plain stores,
+// so concurrent CTAs still race as in Hogwild) and refreshes its copy.
+// Coordinates of cached rows arrive remapped to -(slot + 1).
+//
+// DELTA = true: the per-nonzero step is written to p.delta for the
 // deterministic batch reduction; A is not modified.
 template <int N, int K, int MATH, bool DELTA>
 __global__ void __launch_bounds__(256) k_factor(const EpochArgs p) {
   extern __shared__ __align__(16) float smem[];
-  constexpr int CPL = K / 4;
-  constexpr int TW = Prod<K, MATH>::WORDS;
+  using L = FactorSmem<N, K, MATH>;
   fill_tables<N, K, MATH>(smem, p, true);
+  const bool cache = !DELTA && p.hot_cap > 0;
+  float *rep = cache ? smem + 2 * N * L::TW : nullptr;
+  unsigned char *dirty = cache ? reinterpret_cast<unsigned char *>(rep + size_t(N) * p.hot_cap * K) : nullptr;
+  if (cache) {
+    cache_refresh<N, K>(p, rep);
+    for (int e = threadIdx.x; e < N * p.hot_cap; e += blockDim.x) dirty[e] = 0;
+  }
   __syncthreads();
 
   const int lane = threadIdx.x & 31;
-  const int t = lane & 3;
-  const int64_t warp = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
-  const int64_t nwarps = (int64_t(gridDim.x) * blockDim.x) >> 5;
+  const int wpc = blockDim.x >> 5;
   const int64_t ntiles = (p.end - p.begin + FT_TILE - 1) / FT_TILE;
-
-  for (int64_t tile = warp; tile < ntiles; tile += nwarps) {
-    Front<N, K, MATH, false> f;
-    f.load(p, p.begin + tile * FT_TILE, lane, true);
-    f.compute(smem, TW, lane);
-    float e[2];
-    e[0] = f.x[0] - f.xhat[0];
-    e[1] = f.x[1] - f.xhat[1];
-    const bool bad = (f.valid[0] && !isfinite(e[0])) || (f.valid[1] && !isfinite(e[1]));
-    if (__any_sync(FULL, bad) && lane == 0) atomicOr(p.err, ERRBIT_NONFINITE);
-#pragma unroll
-    for (int n = 0; n < N; ++n) {
-      float d[2][CPL], pp[2][CPL];
-      f.leave_one_out(n, d);
-      Prod<K, MATH>::run(d, smem + (N + n) * TW, pp, lane);
-#pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        if (!f.valid[h]) continue;
-        float out[CPL];
-        if constexpr (DELTA) {
-#pragma unroll
-          for (int q = 0; q < CPL; ++q) out[q] = e[h] * pp[h][q] - p.lam * f.a[n][h][q];
-          float *dst = p.delta + (f.m[h] - p.begin) * p.sumJ + p.offJ[n] + CPL * t;
-#pragma unroll
-          for (int q = 0; q < CPL; ++q)
-            if (CPL * t + q < p.J[n]) dst[q] = out[q];
-        } else {
-          const float lr = p.scale[n] ? p.lr * __ldg(p.scale[n] + f.row[n][h]) : p.lr;
-#pragma unroll
-          for (int q = 0; q < CPL; ++q)
-            out[q] = fmaf(lr, fmaf(e[h], pp[h][q], -p.lam * f.a[n][h][q]), f.a[n][h][q]);
-          store_chunk<K>(p.A[n], f.row[n][h], p.J[n], t, (p.vecmask >> n) & 1, out);
-        }
-      }
+  if (!cache) {
+    const int64_t warp = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = (int64_t(gridDim.x) * blockDim.x) >> 5;
+    for (int64_t tile = warp; tile < ntiles; tile += nwarps)
+      factor_tile<N, K, MATH, DELTA>(p, smem, nullptr, nullptr, tile, lane);
+    return;
+  }
+  // CTA tile c = warp tiles [c * wpc, c * wpc + wpc); CTA b takes c = b, b + G, ...
+  const int64_t nct = (ntiles + wpc - 1) / wpc;
+  const int64_t G = gridDim.x;
+  const int W = p.hot_window > 0 ? p.hot_window : 1;
+  for (int64_t c0 = blockIdx.x; c0 < nct; c0 += G * W) {
+    for (int k = 0; k < W; ++k) {
+      const int64_t c = c0 + k * G;
+      if (c >= nct) break;
+      const int64_t tile = c * wpc + (threadIdx.x >> 5);
+      if (tile < ntiles) factor_tile<N, K, MATH, false>(p, smem, rep, dirty, tile, lane);
+    }
+    __syncthreads();
+    cache_write_back<N, K>(p, rep, dirty);
+    if (c0 + G * W < nct) {
+      __syncthreads();
+      cache_refresh<N, K>(p, rep);
+      __syncthreads();
     }
   }
 }

@@ -21,7 +21,7 @@ ft::KernelSet make_set() {
   s.factor = reinterpret_cast<const void *>(&ft::k_factor<N, FT_K, FT_MATH, false>);
   s.factor_delta = reinterpret_cast<const void *>(&ft::k_factor<N, FT_K, FT_MATH, true>);
   s.core = reinterpret_cast<const void *>(&ft::k_core<N, FT_K, FT_MATH>);
-  s.factor_smem = ft::FactorSmem<N, FT_K, FT_MATH>::bytes();
+  s.factor_smem = ft::FactorSmem<N, FT_K, FT_MATH>::tables();
   s.core_smem = ft::CoreSmem<N, FT_K, FT_MATH>::bytes();
   s.core_threads = 32 * ft::CoreSmem<N, FT_K, FT_MATH>::WARPS;
   return s;

@@ -11,7 +11,7 @@ struct KernelSet {
   const void *factor = nullptr;        // Hogwild factor pass
   const void *factor_delta = nullptr;  // deterministic factor pass (writes per-nonzero steps)
   const void *core = nullptr;          // core-gradient pass
-  size_t factor_smem = 0;
+  size_t factor_smem = 0;              // tables only; the hot-row cache adds to it
   size_t core_smem = 0;
   int core_threads = 256;
 };

@@ -42,7 +42,8 @@ class FtError(RuntimeError):
 class ft_config(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("scatter", ctypes.c_int),
                 ("det_batch", ctypes.c_int64), ("blocks_per_sm", ctypes.c_int),
-                ("reserved", ctypes.c_int * 7)]
+                ("hot_rows", ctypes.c_int), ("hot_window", ctypes.c_int),
+                ("hot_min_count", ctypes.c_int), ("reserved", ctypes.c_int * 4)]
 
 
 _lib = None
@@ -108,13 +109,20 @@ def _stream(stream) -> int:
     return stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
 
 
-def make_config(precision="fp32", scatter="hogwild", det_batch=4096, blocks_per_sm=0) -> ft_config:
+def make_config(precision="fp32", scatter="hogwild", det_batch=4096, blocks_per_sm=0,
+                hot_rows=None, hot_window=None, hot_min_count=None) -> ft_config:
     c = ft_config()
     load().ft_config_default(ctypes.byref(c))
     c.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
     c.scatter = SCATTERS[scatter] if isinstance(scatter, str) else int(scatter)
     c.det_batch = int(det_batch)
     c.blocks_per_sm = int(blocks_per_sm)
+    if hot_rows is not None:
+        c.hot_rows = int(hot_rows)
+    if hot_window is not None:
+        c.hot_window = int(hot_window)
+    if hot_min_count is not None:
+        c.hot_min_count = int(hot_min_count)
     return c
 
 
@@ -199,7 +207,7 @@ class FastTuckerPlus:
     """
 
     def __init__(self, idx, vals, A, B, precision="fp32", scatter="hogwild", det_batch=4096,
-                 blocks_per_sm=0, stream=None):
+                 blocks_per_sm=0, stream=None, hot_rows=None, hot_window=None, hot_min_count=None):
         N = len(A)
         if not (len(idx) == len(B) == N):
             raise ValueError("idx, A and B need one entry per mode")
@@ -214,7 +222,8 @@ class FastTuckerPlus:
         self.J = [int(a.shape[1]) for a in A]
         self.R = int(B[0].shape[1])
         self.nnz = int(vals.numel())
-        self.cfg = make_config(precision, scatter, det_batch, blocks_per_sm)
+        self.cfg = make_config(precision, scatter, det_batch, blocks_per_sm, hot_rows, hot_window,
+                               hot_min_count)
         ws = ft_workspace_size(self.I, self.J, self.R, self.nnz, self.cfg)
         self.workspace = torch.empty(max(ws, 256), dtype=torch.uint8, device=vals.device)
         self.ctx = ft_init(self.I, self.J, self.R, self.idx, vals, self.A, self.B, self.workspace,

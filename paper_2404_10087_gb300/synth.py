@@ -182,6 +182,10 @@ WORKLOADS = {
     "netflix_shaped_zipf_1e8": Workload(
         name="netflix_shaped_zipf_1e8", I=(480_000, 18_000, 2_200), nnz=100_000_000,
         J=(16, 16, 16), R=16, dist="zipf", zipf_s=1.1, planted_std=0.25, ratings=True),
+    # the same shape and size without popularity skew (no hot rows)
+    "netflix_shaped_uniform_1e8": Workload(
+        name="netflix_shaped_uniform_1e8", I=(480_000, 18_000, 2_200), nnz=100_000_000,
+        J=(16, 16, 16), R=16, dist="uniform", planted_std=0.25, ratings=True),
     "order4_zipf_2e8": Workload(
         name="order4_zipf_2e8", I=(1_000_000, 1_000_000, 100_000, 1_000), nnz=200_000_000,
         J=(32, 32, 32, 32), R=32, dist="zipf", zipf_s=1.05, noise_std=0.05),
