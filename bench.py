@@ -356,7 +356,7 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--precision", choices=["fp32", "tf32", "bf16"], default="fp32")
+    ap.add_argument("--precision", choices=["fp32", "tf32", "bf16"], default="bf16")
     ap.add_argument("--cpu-sample", type=int, default=2_000_000)
     ap.add_argument("--ref-sample", type=int, default=1_000_000)
     ap.add_argument("--no-cpu-baseline", action="store_true")

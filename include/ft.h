@@ -89,19 +89,20 @@ typedef struct {
   int64_t det_batch;   /* batch size S of FT_DETERMINISTIC (>= 1) */
   int blocks_per_sm;   /* persistent CTAs per SM; 0 = from the occupancy API */
   /* FT_HOGWILD only: shared-memory write-back cache of the most frequent rows
-   * of every mode.  Each CTA keeps hot_rows rows per mode in shared memory,
-   * updates them there, and writes its dirty rows back (plain stores, so CTAs
-   * still race as in Hogwild) and refreshes them every hot_window CTA tiles
-   * (8 warps x 16 nonzeros).  Only rows with at least hot_min_count training
-   * nonzeros are cached.  hot_rows: -1 = as many as 64 KB hold, 0 = off. */
+   * of the tensor (ranked over all modes by their number of training
+   * nonzeros).  Each CTA keeps hot_rows rows in shared memory, updates them
+   * there, and every hot_window CTA tiles (8 warps x 16 nonzeros) writes its
+   * dirty rows back (plain stores, so CTAs still race as in Hogwild) and
+   * refreshes its copy.  Only rows with at least hot_min_count training
+   * nonzeros are cached.  hot_rows: -1 = as many as 96 KB hold, 0 = off. */
   int hot_rows;
-  int hot_window;      /* >= 1; default 16 */
+  int hot_window;      /* >= 1; default 64 */
   int hot_min_count;   /* >= 1; default 2 */
   int reserved[4];     /* must be zero */
 } ft_config;
 
 /* Fill *cfg with the defaults: FT_FP32, FT_HOGWILD, det_batch 4096, automatic
- * grid, hot_rows -1, hot_window 16, hot_min_count 2. */
+ * grid, hot_rows -1, hot_window 64, hot_min_count 2. */
 void ft_config_default(ft_config *cfg);
 
 /* Bytes of device workspace needed by ft_init for this problem (host call;

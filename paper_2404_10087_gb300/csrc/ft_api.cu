@@ -182,7 +182,7 @@ struct Plan {
   ft::EvalSet es;
   int grid_factor = 0, grid_core = 0, grid_eval = 0;
   int64_t det_S = 0, nbatches = 0;
-  int hot_cap = 0;                   // cache slots per mode (0 = no cache)
+  int hot_cap = 0;                   // cache slots, all modes (0 = no cache)
   size_t factor_smem = 0;            // Hogwild pass, tables + cache
   // workspace offsets
   size_t off_err = 0, off_out = 0, off_partial = 0, off_errpart = 0, off_delta = 0;
@@ -190,7 +190,9 @@ struct Plan {
   size_t off_remap = 0, off_hot = 0, off_counts = 0, total = 0;
 };
 
-constexpr size_t kHotCacheBytes = 64 * 1024;
+// Shared memory of the hot-row cache: with two 256-thread CTAs per SM (the
+// register limit of the factor pass) each CTA can hold about 100 KB.
+constexpr size_t kHotCacheBytes = 96 * 1024;
 constexpr size_t kMaxSmem = 227 * 1024;
 
 ft_status cuda_status(cudaError_t e) { return e == cudaSuccess ? FT_OK : FT_ERR_CUDA; }
@@ -257,15 +259,18 @@ ft_status make_plan(int N, const int64_t *I, const int *J, int R, int64_t nnz, c
   for (int n = 0; n < N; ++n) maxI = std::max(maxI, I[n]);
   p->hot_cap = 0;
   if (c.scatter == FT_HOGWILD && c.hot_rows != 0 && nnz > 0) {
-    int64_t cap = c.hot_rows > 0 ? c.hot_rows : int64_t(kHotCacheBytes / (size_t(N) * K * sizeof(float)));
-    cap = std::min(cap, maxI);
-    const size_t per_slot = size_t(N) * K * sizeof(float) + N;
+    const size_t per_slot = size_t(K) * sizeof(float) + 1;
+    int64_t sumI = 0;
+    for (int n = 0; n < N; ++n) sumI += I[n];
+    int64_t cap = c.hot_rows > 0 ? c.hot_rows : int64_t(kHotCacheBytes / per_slot);
+    cap = std::min(cap, sumI);
     const int64_t fit = int64_t((kMaxSmem - p->ks.factor_smem - 64) / per_slot);
     if (cap > fit) return FT_ERR_ARG;
     p->hot_cap = int(std::max<int64_t>(cap, 0));
   }
-  p->factor_smem = p->ks.factor_smem + size_t(N) * p->hot_cap * K * sizeof(float) +
-                   ((size_t(N) * p->hot_cap + 15) / 16) * 16;
+  p->factor_smem = p->ks.factor_smem + size_t(p->hot_cap) * K * sizeof(float) +
+                   ((size_t(p->hot_cap) + 15) / 16) * 16;
+  (void)maxI;
   const int occ_f = occupancy(p->ks.factor, 256, p->factor_smem);
   const int occ_d = occupancy(p->ks.factor_delta, 256, p->ks.factor_smem);
   const int occ_c = occupancy(p->ks.core, p->ks.core_threads, p->ks.core_smem);
@@ -286,7 +291,7 @@ ft_status make_plan(int N, const int64_t *I, const int *J, int R, int64_t nnz, c
     int64_t sumI = 0;
     for (int n = 0; n < N; ++n) sumI += I[n];
     p->off_remap = off;  off += align_up(sizeof(int32_t) * size_t(N) * nnz);
-    p->off_hot = off;    off += align_up(sizeof(int32_t) * size_t(N) * p->hot_cap);
+    p->off_hot = off;    off += align_up(sizeof(int32_t) * size_t(p->hot_cap));
     p->off_counts = off; off += align_up(sizeof(int32_t) * size_t(sumI));
   }
   if (c.scatter == FT_DETERMINISTIC) {
@@ -313,7 +318,7 @@ struct ft_ctx {
   char *ws = nullptr;
   unsigned vecmask = 0;
   std::vector<int64_t> seg_lo[FT_MAXN];  // per mode: first segment of each batch (+ end)
-  int hot_count[FT_MAXN] = {0};          // cached rows per mode (Hogwild)
+  int hot_base[FT_MAXN + 1] = {0};       // cache slots of mode n: [base[n], base[n+1])
   bool hot_active = false;
   int64_t launches = 0;
 };
@@ -437,28 +442,38 @@ ft_status build_hot_cache(ft_ctx *c, cudaStream_t st) {
       cudaStreamSynchronize(st) != cudaSuccess)
     return FT_ERR_CUDA;
   std::vector<int32_t> slot_of(size_t(sumI), -1);
-  std::vector<int32_t> hot(size_t(p.N) * p.hot_cap, 0);
-  bool any = false;
+  // the hot_cap most frequent rows of the whole tensor (ties: lower mode, then
+  // lower row), grouped by mode into contiguous slot ranges
+  struct Cand { int32_t count; int32_t n; int32_t r; };
+  std::vector<Cand> cand;
   off = 0;
   for (int n = 0; n < p.N; ++n) {
-    std::vector<int32_t> cand;
     for (int64_t r = 0; r < p.I[n]; ++r)
-      if (counts[size_t(off + r)] >= p.cfg.hot_min_count) cand.push_back(int32_t(r));
-    const size_t k = std::min(cand.size(), size_t(p.hot_cap));
-    std::partial_sort(cand.begin(), cand.begin() + k, cand.end(), [&](int32_t a, int32_t b) {
-      const int32_t ca_ = counts[size_t(off + a)], cb = counts[size_t(off + b)];
-      return ca_ != cb ? ca_ > cb : a < b;
-    });
-    for (size_t q = 0; q < k; ++q) {
-      hot[size_t(n) * p.hot_cap + q] = cand[q];
-      slot_of[size_t(off + cand[q])] = int32_t(q);
-    }
-    c->hot_count[n] = int(k);
-    any = any || k > 0;
+      if (counts[size_t(off + r)] >= p.cfg.hot_min_count)
+        cand.push_back(Cand{counts[size_t(off + r)], int32_t(n), int32_t(r)});
     off += p.I[n];
   }
-  c->hot_active = any;
-  if (!any) return FT_OK;
+  const size_t k = std::min(cand.size(), size_t(p.hot_cap));
+  std::partial_sort(cand.begin(), cand.begin() + k, cand.end(), [](const Cand &a, const Cand &b) {
+    if (a.count != b.count) return a.count > b.count;
+    return a.n != b.n ? a.n < b.n : a.r < b.r;
+  });
+  cand.resize(k);
+  std::sort(cand.begin(), cand.end(), [](const Cand &a, const Cand &b) {
+    return a.n != b.n ? a.n < b.n : a.r < b.r;
+  });
+  std::vector<int32_t> hot(std::max<size_t>(k, 1), 0);
+  int64_t mode_off[FT_MAXN + 1] = {0};
+  for (int n = 0; n < p.N; ++n) mode_off[n + 1] = mode_off[n] + p.I[n];
+  for (int n = 0; n <= p.N; ++n) c->hot_base[n] = 0;
+  for (size_t q = 0; q < k; ++q) {
+    hot[q] = cand[q].r;
+    slot_of[size_t(mode_off[cand[q].n] + cand[q].r)] = int32_t(q);
+    c->hot_base[cand[q].n + 1] += 1;
+  }
+  for (int n = 0; n < p.N; ++n) c->hot_base[n + 1] += c->hot_base[n];
+  c->hot_active = k > 0;
+  if (k == 0) return FT_OK;
   int32_t *d_hot = ws_ptr<int32_t>(c, p.off_hot);
   if (cudaMemcpyAsync(d_hot, hot.data(), sizeof(int32_t) * hot.size(), cudaMemcpyHostToDevice, st) !=
           cudaSuccess ||
@@ -505,7 +520,7 @@ void ft_config_default(ft_config *cfg) {
   cfg->det_batch = 4096;
   cfg->blocks_per_sm = 0;
   cfg->hot_rows = -1;
-  cfg->hot_window = 16;
+  cfg->hot_window = 64;
   cfg->hot_min_count = 2;
 }
 
@@ -591,11 +606,9 @@ ft_status ft_epoch_factors(ft_ctx *c, float lr_a, float lambda_a, const float *c
     for (int n = 0; n < p.N; ++n) a.scale[n] = row_step_scale[n];
   if (p.cfg.scatter == FT_HOGWILD) {
     if (c->hot_active) {
-      for (int n = 0; n < p.N; ++n) {
-        a.idx[n] = ws_ptr<int32_t>(c, p.off_remap) + size_t(n) * p.nnz;
-        a.hot_rows[n] = ws_ptr<int32_t>(c, p.off_hot) + size_t(n) * p.hot_cap;
-        a.hot_count[n] = c->hot_count[n];
-      }
+      for (int n = 0; n < p.N; ++n) a.idx[n] = ws_ptr<int32_t>(c, p.off_remap) + size_t(n) * p.nnz;
+      for (int n = 0; n <= p.N; ++n) a.hot_base[n] = c->hot_base[n];
+      a.hot_rows = ws_ptr<int32_t>(c, p.off_hot);
       a.hot_cap = p.hot_cap;
       a.hot_window = p.cfg.hot_window;
     }

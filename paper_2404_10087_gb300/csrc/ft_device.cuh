@@ -64,12 +64,20 @@ struct EpochArgs {
   double *err_partial;              // errors: per-CTA (sum e^2, sum |e|)
   int *err;                         // latched error word
   // Hot-row cache of the Hogwild factor pass (see k_factor): idx[n][m] < 0
-  // addresses slot -idx - 1 of mode n, whose global row is hot_rows[n][slot].
-  const int32_t *hot_rows[FT_MAXN];
-  int hot_count[FT_MAXN];           // slots in use per mode
-  int hot_cap;                      // slots per mode in shared memory (0 = no cache)
+  // addresses cache slot -idx - 1; slots [hot_base[n], hot_base[n + 1]) hold
+  // rows of mode n, and hot_rows[slot] is the slot's row.
+  const int32_t *hot_rows;
+  int hot_base[FT_MAXN + 1];
+  int hot_cap;                      // slots in shared memory (0 = no cache)
   int hot_window;                   // CTA tiles between write-back/refresh
 };
+
+// Mode of a cache slot.
+__device__ __forceinline__ int slot_mode(const EpochArgs &p, int slot, int N) {
+  int n = 0;
+  while (n + 1 < N && slot >= p.hot_base[n + 1]) ++n;
+  return n;
+}
 
 // ------------------------------------------------------------- small helpers
 __device__ __forceinline__ uint32_t to_tf32(float f) {
@@ -333,7 +341,7 @@ struct Front {
       for (int n = 0; n < N; ++n) {
         const int32_t v = row[n][h];
         if (rep != nullptr && v < 0) {
-          ok = ok && (-v - 1) < p.hot_count[n];
+          ok = ok && (-v - 1) >= p.hot_base[n] && (-v - 1) < p.hot_base[n + 1];
           row[n][h] = -v - 1;
           hot |= 1u << (2 * n + h);
         } else {
@@ -356,7 +364,7 @@ struct Front {
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
         if ((hot >> (2 * n + h)) & 1u) {
-          const float *src = rep + (size_t(n) * p.hot_cap + row[n][h]) * K + CPL * t;
+          const float *src = rep + size_t(row[n][h]) * K + CPL * t;
 #pragma unroll
           for (int w = 0; w < CPL; w += 4) {
             const float4 f4 = *reinterpret_cast<const float4 *>(src + w);
@@ -406,14 +414,11 @@ struct Front {
 
 // Shared-memory layout of the factor kernel: for each mode the a.B table,
 // then for each mode the d.B^T table, then (Hogwild pass) the hot-row cache
-// [N][hot_cap][K] floats and its dirty flags [N][hot_cap] bytes.
+// [hot_cap][K] floats and its dirty flags [hot_cap] bytes.
 template <int N, int K, int MATH>
 struct FactorSmem {
   static constexpr int TW = Prod<K, MATH>::WORDS;
   static constexpr size_t tables() { return size_t(2) * N * TW * sizeof(float); }
-  static constexpr size_t bytes(int hot_cap) {
-    return tables() + size_t(N) * hot_cap * K * sizeof(float) + ((size_t(N) * hot_cap + 15) / 16) * 16;
-  }
 };
 
 template <int N, int K, int MATH>
@@ -430,13 +435,12 @@ __device__ __forceinline__ void fill_tables(float *smem, const EpochArgs &p, boo
 // dirty slots back and clear their flags.
 template <int N, int K>
 __device__ void cache_refresh(const EpochArgs &p, float *rep) {
-  for (int e = threadIdx.x; e < N * p.hot_cap * (K / 4); e += blockDim.x) {
-    const int n = e / (p.hot_cap * (K / 4));
-    const int rem = e % (p.hot_cap * (K / 4));
-    const int slot = rem / (K / 4), j0 = 4 * (rem % (K / 4));
+  for (int e = threadIdx.x; e < p.hot_cap * (K / 4); e += blockDim.x) {
+    const int slot = e / (K / 4), j0 = 4 * (e % (K / 4));
+    const int n = slot_mode(p, slot, N);
     float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (slot < p.hot_count[n] && j0 < p.J[n]) {
-      const float *src = p.A[n] + int64_t(__ldg(p.hot_rows[n] + slot)) * p.J[n] + j0;
+    if (slot < p.hot_base[N] && j0 < p.J[n]) {
+      const float *src = p.A[n] + int64_t(__ldg(p.hot_rows + slot)) * p.J[n] + j0;
       if (((p.vecmask >> n) & 1) != 0) {
         v = __ldcg(reinterpret_cast<const float4 *>(src));
       } else {
@@ -446,19 +450,18 @@ __device__ void cache_refresh(const EpochArgs &p, float *rep) {
         if (j0 + 3 < p.J[n]) v.w = __ldcg(src + 3);
       }
     }
-    *reinterpret_cast<float4 *>(rep + (size_t(n) * p.hot_cap + slot) * K + j0) = v;
+    *reinterpret_cast<float4 *>(rep + size_t(slot) * K + j0) = v;
   }
 }
 
 template <int N, int K>
 __device__ void cache_write_back(const EpochArgs &p, const float *rep, unsigned char *dirty) {
-  for (int e = threadIdx.x; e < N * p.hot_cap * (K / 4); e += blockDim.x) {
-    const int n = e / (p.hot_cap * (K / 4));
-    const int rem = e % (p.hot_cap * (K / 4));
-    const int slot = rem / (K / 4), j0 = 4 * (rem % (K / 4));
-    if (slot >= p.hot_count[n] || j0 >= p.J[n] || !dirty[n * p.hot_cap + slot]) continue;
-    const float4 v = *reinterpret_cast<const float4 *>(rep + (size_t(n) * p.hot_cap + slot) * K + j0);
-    float *dst = p.A[n] + int64_t(__ldg(p.hot_rows[n] + slot)) * p.J[n] + j0;
+  for (int e = threadIdx.x; e < p.hot_cap * (K / 4); e += blockDim.x) {
+    const int slot = e / (K / 4), j0 = 4 * (e % (K / 4));
+    const int n = slot_mode(p, slot, N);
+    if (slot >= p.hot_base[N] || j0 >= p.J[n] || !dirty[slot]) continue;
+    const float4 v = *reinterpret_cast<const float4 *>(rep + size_t(slot) * K + j0);
+    float *dst = p.A[n] + int64_t(__ldg(p.hot_rows + slot)) * p.J[n] + j0;
     if (((p.vecmask >> n) & 1) != 0) {
       __stcg(reinterpret_cast<float4 *>(dst), v);
     } else {
@@ -469,7 +472,7 @@ __device__ void cache_write_back(const EpochArgs &p, const float *rep, unsigned 
     }
   }
   __syncthreads();
-  for (int e = threadIdx.x; e < N * p.hot_cap; e += blockDim.x) dirty[e] = 0;
+  for (int e = threadIdx.x; e < p.hot_cap; e += blockDim.x) dirty[e] = 0;
 }
 
 // One factor-phase tile (Algorithm 4): C = A_Psi B, D = *_{k != n} C,
@@ -511,18 +514,18 @@ __device__ __forceinline__ void factor_tile(const EpochArgs &p, const float *tab
         const bool is_hot = (f.hot >> (2 * n + h)) & 1u;
         float lr = p.lr;
         if (p.scale[n]) {
-          const int64_t grow = is_hot ? int64_t(__ldg(p.hot_rows[n] + f.row[n][h])) : int64_t(f.row[n][h]);
+          const int64_t grow = is_hot ? int64_t(__ldg(p.hot_rows + f.row[n][h])) : int64_t(f.row[n][h]);
           lr *= __ldg(p.scale[n] + grow);
         }
 #pragma unroll
         for (int q = 0; q < CPL; ++q)
           out[q] = fmaf(lr, fmaf(e[h], pp[h][q], -p.lam * f.a[n][h][q]), f.a[n][h][q]);
         if (is_hot) {
-          float *dst = rep + (size_t(n) * p.hot_cap + f.row[n][h]) * K + CPL * t;
+          float *dst = rep + size_t(f.row[n][h]) * K + CPL * t;
 #pragma unroll
           for (int w = 0; w < CPL; w += 4)
             *reinterpret_cast<float4 *>(dst + w) = make_float4(out[w], out[w + 1], out[w + 2], out[w + 3]);
-          if (t == 0) dirty[n * p.hot_cap + f.row[n][h]] = 1;
+          if (t == 0) dirty[f.row[n][h]] = 1;
         } else {
           store_chunk<K>(p.A[n], f.row[n][h], p.J[n], t, (p.vecmask >> n) & 1, out);
         }
@@ -543,7 +546,8 @@ __device__ __forceinline__ void factor_tile(const EpochArgs &p, const float *tab
 // the CTA's warps read and update the cached copy, and every hot_window CTA
 // tiles the CTA writes its dirty rows back to global memory (plain stores,
 // so concurrent CTAs still race as in Hogwild) and refreshes its copy.
-// Coordinates of cached rows arrive remapped to -(slot + 1).
+// Coordinates of cached rows arrive remapped to -(slot + 1); the slots are
+// shared by all modes and go to the most frequent rows of the tensor.
 //
 // DELTA = true: the per-nonzero step is written to p.delta for the
 // deterministic batch reduction; A is not modified.
@@ -554,10 +558,10 @@ __global__ void __launch_bounds__(256) k_factor(const EpochArgs p) {
   fill_tables<N, K, MATH>(smem, p, true);
   const bool cache = !DELTA && p.hot_cap > 0;
   float *rep = cache ? smem + 2 * N * L::TW : nullptr;
-  unsigned char *dirty = cache ? reinterpret_cast<unsigned char *>(rep + size_t(N) * p.hot_cap * K) : nullptr;
+  unsigned char *dirty = cache ? reinterpret_cast<unsigned char *>(rep + size_t(p.hot_cap) * K) : nullptr;
   if (cache) {
     cache_refresh<N, K>(p, rep);
-    for (int e = threadIdx.x; e < N * p.hot_cap; e += blockDim.x) dirty[e] = 0;
+    for (int e = threadIdx.x; e < p.hot_cap; e += blockDim.x) dirty[e] = 0;
   }
   __syncthreads();
 
