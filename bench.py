@@ -146,7 +146,7 @@ def make_workload(device, nnz=None, name=WORKLOAD):
     allidx = [d.idx[n].contiguous() for n in range(N)]
     zeros = torch.zeros(d.idx.shape[1], dtype=torch.float32, device=device)
     pm = ft.FastTuckerPlus(allidx, zeros, [a.contiguous() for a in d.planted_A],
-                           [b.contiguous() for b in d.planted_B])
+                           [b.contiguous() for b in d.planted_B], hot_rows=0)
     pred = pm.predict(allidx)
     pm.close()
     del zeros
@@ -353,7 +353,7 @@ def run_reference(args, rank, world):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--precision", choices=["fp32", "tf32", "bf16"], default="bf16")
