@@ -143,6 +143,34 @@ ft_status ft_epoch_core(ft_ctx *ctx, float lr_b, float lambda_b, void *stream);
  * n = 0..N-1, each J_n x R row-major, concatenated. */
 ft_status ft_core_grad(ft_ctx *ctx, float *G_out, void *stream);
 
+/* The core gradient of ft_core_grad without a context and without any
+ * allocation, for callers that cannot call cudaMalloc: for example code whose
+ * device memory is owned by another allocator (a framework or service that
+ * has reserved the device's memory in its own pool and forbids allocations
+ * outside it), or a caller that cannot keep a context and its workspace alive
+ * between calls.  The paper has no counterpart; this is a library service.
+ *   idx, vals, A, B: as for ft_init (device data; host arrays of N device
+ *   pointers); precision: FT_FP32 | FT_TF32 | FT_BF16; G_out (device)
+ *   receives G^(n) = sum (xhat - x) a^(n)T d^(n), each J_n x R row-major,
+ *   concatenated over n.
+ * Scratch: the call needs no workspace.  Its scratch (the per-CTA partial
+ * sums of the core pass) lives in one 8 MiB device array compiled into the
+ * library, which every GPU that loads the library holds until the process
+ * exits.  Calls that would need more than that (more CTAs times N * K * K
+ * partials than fit) return FT_ERR_WORKSPACE; on a GB300 every supported
+ * shape fits.  The first call on a device looks up the array's device address
+ * with that device current (make that first call before any stream capture).
+ * Every call shares the array and overwrites it: calls that overlap on the
+ * GPU (on different streams or host threads) race and corrupt each other's
+ * results, so serialise them.
+ * The result equals ft_core_grad's for the same inputs (same grid and fixed
+ * summation order).  Synchronises the stream to report bad coordinates
+ * (FT_ERR_INDEX) or non-finite residuals (FT_ERR_NONFINITE). */
+ft_status ft_core_grad_noalloc(int N, const int64_t *I, const int *J, int R, int64_t nnz,
+                               const int32_t *const *idx, const float *vals,
+                               const float *const *A, const float *const *B, int precision,
+                               float *G_out, void *stream);
+
 /* Predictions xhat (float32) of n coordinates (idx: host array of N device
  * pointers; out: device, n floats) with the context's current A and B. */
 ft_status ft_predict(ft_ctx *ctx, int64_t n, const int32_t *const *idx, float *out,

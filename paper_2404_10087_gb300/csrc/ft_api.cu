@@ -7,6 +7,7 @@
 #include <cmath>
 #include <cstdint>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <vector>
 
@@ -691,6 +692,107 @@ ft_status ft_epoch_core(ft_ctx *c, float lr_b, float lambda_b, void *stream) {
 ft_status ft_core_grad(ft_ctx *c, float *G_out, void *stream) {
   if (!c || !G_out) return FT_ERR_ARG;
   return core_pass(c, 0.f, 0.f, G_out, 0, static_cast<cudaStream_t>(stream));
+}
+
+// ---------------------------------------------- core gradient, no allocation
+// Scratch of ft_core_grad_noalloc: a 256-byte error word followed by the
+// per-CTA (sum, compensation) partials of the core-gradient kernel.  It is a
+// file-scope device array, so every GPU that loads this library holds it
+// until the process exits, and every call shares it.
+#define FT_NOALLOC_SCRATCH_BYTES (8u << 20)
+static __device__ __align__(256) unsigned char g_noalloc_scratch[FT_NOALLOC_SCRATCH_BYTES];
+
+namespace {
+constexpr int kNoallocMaxDevices = 64;
+std::mutex g_noalloc_lock;
+void *g_noalloc_addr[kNoallocMaxDevices] = {nullptr};
+
+// Device address of the scratch array on the current device.  In host code
+// the array's name is only a host-side stand-in, so the address is looked up
+// once per device (with that device current) and cached.
+ft_status noalloc_scratch(int dev, void **out) {
+  if (dev < 0 || dev >= kNoallocMaxDevices) return FT_ERR_CUDA;
+  std::lock_guard<std::mutex> guard(g_noalloc_lock);
+  if (g_noalloc_addr[dev] == nullptr) {
+    void *ptr = nullptr;
+    if (cudaGetSymbolAddress(&ptr, g_noalloc_scratch) != cudaSuccess || ptr == nullptr) return FT_ERR_CUDA;
+    g_noalloc_addr[dev] = ptr;
+  }
+  *out = g_noalloc_addr[dev];
+  return FT_OK;
+}
+}  // namespace
+
+ft_status ft_core_grad_noalloc(int N, const int64_t *I, const int *J, int R, int64_t nnz,
+                               const int32_t *const *idx, const float *vals, const float *const *A,
+                               const float *const *B, int precision, float *G_out, void *stream) {
+  if (!I || !J || !G_out || (nnz > 0 && (!idx || !vals)) || !A || !B) return FT_ERR_ARG;
+  ft_config cfg;
+  ft_config_default(&cfg);
+  cfg.precision = precision;
+  cfg.hot_rows = 0;
+  Plan p;
+  ft_status s = make_plan(N, I, J, R, nnz, &cfg, &p);
+  if (s != FT_OK) return s;
+  const size_t need = 256 + sizeof(float) * 2 * size_t(p.grid_core) * N * p.K * p.K;
+  if (need > FT_NOALLOC_SCRATCH_BYTES) return FT_ERR_WORKSPACE;
+  void *scratch = nullptr;
+  s = noalloc_scratch(p.dev, &scratch);
+  if (s != FT_OK) return s;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  int *err = static_cast<int *>(scratch);
+  if (cudaMemsetAsync(err, 0, sizeof(int), st) != cudaSuccess) return FT_ERR_CUDA;
+
+  ft::EpochArgs a;
+  memset(&a, 0, sizeof(a));
+  for (int n = 0; n < N; ++n) {
+    if ((nnz > 0 && !idx[n]) || !A[n] || !B[n]) return FT_ERR_ARG;
+    a.idx[n] = nnz > 0 ? idx[n] : nullptr;
+    a.A[n] = const_cast<float *>(A[n]);  // read only in the core pass
+    a.B[n] = B[n];
+    a.I[n] = I[n];
+    a.J[n] = J[n];
+    a.offJ[n] = p.offJ[n];
+    if (J[n] == p.K && (reinterpret_cast<uintptr_t>(A[n]) % 16) == 0) a.vecmask |= 1u << n;
+  }
+  a.R = R;
+  a.sumJ = p.sumJ;
+  a.vals = vals;
+  a.begin = 0;
+  a.end = nnz;
+  a.err = err;
+  a.partial = reinterpret_cast<float *>(static_cast<char *>(scratch) + 256);
+  void *argv_core[] = {&a};
+  if (cudaLaunchKernel(p.ks.core, dim3(p.grid_core), dim3(p.ks.core_threads), argv_core, p.ks.core_smem, st) !=
+      cudaSuccess)
+    return FT_ERR_CUDA;
+  FinalizeArgs f;
+  memset(&f, 0, sizeof(f));
+  f.partial = a.partial;
+  f.nparts = p.grid_core;
+  f.N = N;
+  f.K = p.K;
+  f.R = R;
+  int off = 0;
+  for (int n = 0; n < N; ++n) {
+    f.J[n] = J[n];
+    f.offG[n] = off;
+    off += J[n] * R;
+  }
+  f.G_out = G_out;
+  f.update = 0;
+  void *argv_fin[] = {&f};
+  const int total = N * p.K * p.K;
+  if (cudaLaunchKernel(reinterpret_cast<const void *>(&k_finalize), dim3((total + 255) / 256), dim3(256), argv_fin,
+                       0, st) != cudaSuccess)
+    return FT_ERR_CUDA;
+  int h_err = 0;
+  if (cudaMemcpyAsync(&h_err, err, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess)
+    return FT_ERR_CUDA;
+  if (h_err & ft::ERRBIT_INDEX) return FT_ERR_INDEX;
+  if (h_err) return FT_ERR_NONFINITE;
+  return FT_OK;
 }
 
 static ft_status eval_args(ft_ctx *c, int64_t n, const int32_t *const *idx, ft::EpochArgs *a) {

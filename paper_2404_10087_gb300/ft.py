@@ -30,7 +30,7 @@ STATUS = {0: "FT_OK", -1: "FT_ERR_ARG", -2: "FT_ERR_INDEX", -3: "FT_ERR_SHAPE", 
 # Every symbol the header declares (checked by the tests against the library).
 EXPORTS = ["ft_config_default", "ft_workspace_size", "ft_init", "ft_epoch_factors",
            "ft_epoch_core", "ft_core_grad", "ft_predict", "ft_rmse", "ft_check",
-           "ft_launch_count", "ft_destroy", "ft_status_str"]
+           "ft_launch_count", "ft_destroy", "ft_status_str", "ft_core_grad_noalloc"]
 
 
 class FtError(RuntimeError):
@@ -87,6 +87,7 @@ def _declare(lib):
         "ft_launch_count": (I64, [_P]),
         "ft_destroy": (None, [_P]),
         "ft_status_str": (ctypes.c_char_p, [INT]),
+        "ft_core_grad_noalloc": (INT, [INT, _P, _P, INT, I64, _P, _P, _P, _P, INT, _P, _P]),
     }
     for name, (res, args) in sigs.items():
         f = getattr(lib, name)
@@ -163,6 +164,21 @@ def ft_epoch_core(ctx, lr_b, lambda_b, stream=None):
 
 def ft_core_grad(ctx, G_out, stream=None):
     _check(load().ft_core_grad(ctx, G_out.data_ptr(), _stream(stream)), "ft_core_grad")
+
+
+def ft_core_grad_noalloc(idx, vals, A, B, G_out, precision="fp32", stream=None):
+    """Core gradient without a context or workspace (the library's static
+    scratch is used; see include/ft.h).  idx, A, B: lists of device tensors;
+    G_out: device float32 tensor of sum_n J_n * R entries."""
+    N = len(A)
+    I = (ctypes.c_int64 * N)(*[int(a.shape[0]) for a in A])
+    J = (ctypes.c_int * N)(*[int(a.shape[1]) for a in A])
+    R = int(B[0].shape[1])
+    nnz = int(vals.numel())
+    prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+    _check(load().ft_core_grad_noalloc(N, I, J, R, nnz, _ptrs(idx) if nnz else None,
+                                       vals.data_ptr() if nnz else None, _ptrs(A), _ptrs(B), prec,
+                                       G_out.data_ptr(), _stream(stream)), "ft_core_grad_noalloc")
 
 
 def ft_predict(ctx, idx, out, stream=None):
