@@ -136,6 +136,18 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def aggregate_replicas(times_ms, units_per_rank, steps, world, device="cpu"):
+    """Replicas only: every rank trains its own tensor.  The job time is the
+    slowest rank's (max over ranks of each timing) and the value is the units
+    of all ranks over that time: world * units / (times_ms[0] / steps)."""
+    t = torch.tensor([float(v) for v in times_ms], dtype=torch.float64, device=device)
+    if world > 1:
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    out = [float(v) for v in t.cpu()]
+    value = world * units_per_rank / (out[0] / steps / 1e3)
+    return out, value
+
+
 def make_workload(device, nnz=None, name=WORKLOAD):
     """Draw the synthetic tensor on `device`; planted values are computed by the
     library's own predict call, then mapped to integer ratings 1..5 (ratings
@@ -232,12 +244,8 @@ def run_ours(args, rank, world, local_rank):
     torch.cuda.synchronize()
     e2e_ms = te0.elapsed_time(te1) / e2e_steps
 
-    times = torch.tensor([total_ms, e2e_ms], dtype=torch.float64, device=dev)
-    if world > 1:
-        torch.distributed.all_reduce(times, op=torch.distributed.ReduceOp.MAX)
-    total_ms, e2e_ms = float(times[0]), float(times[1])
+    (total_ms, e2e_ms), value = aggregate_replicas([total_ms, e2e_ms], nnz_train, args.steps, world, dev)
     ms_per_step = total_ms / args.steps
-    value = world * nnz_train / (ms_per_step / 1e3)
     if rank != 0:
         return None
 
