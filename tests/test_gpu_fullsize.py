@@ -6,7 +6,8 @@ are computed by the FP64 oracle (never by the CUDA path).  Against the
 oracle:
   * predictions on a 2e5-nonzero sample (FP32, bound-relative 1e-5);
   * the core gradient over all 9e7 training nonzeros (FP32 <= 1e-5 and BF16
-    <= 2e-2 in Frobenius norm), and the core epoch's B;
+    <= 2e-2 in Frobenius norm), and the core epoch's B (its step to the same
+    tolerance, plus the float32 rounding of the stored B);
   * the test-set RMSE and MAE (<= 1e-5);
   * the Hogwild factor pass in the benchmark's configuration (BF16, hot-row
     cache): properties that hold at any size - rows of no training nonzero are
@@ -90,8 +91,11 @@ def test_fullsize_core_gradient_and_epoch(full, oracle_grad, precision, tol):
     for n in range(3):
         b0 = full["B0"][n].double().numpy()
         want = b0 - lr * (oracle_grad[n] / nnz + lam * b0)
-        step_got = gB[n].double().cpu().numpy() - b0
-        assert rel_fro(step_got, want - b0) <= tol, n
+        got = gB[n].double().cpu().numpy()
+        # the step (~1e-4 of B) is compared up to tol plus the float32 rounding
+        # of the stored B (a few ulps of |B|)
+        err = np.linalg.norm(got - want)
+        assert err <= tol * np.linalg.norm(want - b0) + 4 * 2.0 ** -24 * np.linalg.norm(want), n
 
 
 def test_fullsize_errors(full):
