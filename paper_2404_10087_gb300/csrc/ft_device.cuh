@@ -303,6 +303,29 @@ __device__ __forceinline__ void store_chunk(float *__restrict__ An, int64_t row,
   }
 }
 
+// Coordinates and values of one warp tile (loaded a tile ahead of use).
+template <int N>
+struct TileCoords {
+  int64_t m[2];
+  bool valid[2];
+  int32_t row[N][2];
+  float x[2];
+
+  __device__ __forceinline__ void load(const EpochArgs &p, int64_t tile_base, int lane, bool need_x) {
+    const int g = lane >> 2;
+    m[0] = tile_base + g;
+    m[1] = tile_base + g + 8;
+    valid[0] = m[0] < p.end;
+    valid[1] = m[1] < p.end;
+#pragma unroll
+    for (int n = 0; n < N; ++n)
+#pragma unroll
+      for (int h = 0; h < 2; ++h) row[n][h] = valid[h] ? __ldcs(p.idx[n] + m[h]) : 0;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) x[h] = (need_x && valid[h]) ? __ldcs(p.vals + m[h]) : 0.f;
+  }
+};
+
 // ------------------------------------------------------- shared tile front
 // Gathers the tile (a1, a2), forms C^(n) = A_Psi^(n) B^(n) for every mode
 // (Algorithm 4, C step) and the prediction xhat per row (Eq. "fasttucker").
@@ -318,19 +341,29 @@ struct Front {
   float c[N][2][CPL];
   float xhat[2];
 
-  // rep: the CTA's hot-row cache ([N][hot_cap][K] floats) or null.
+  // rep: the CTA's hot-row cache ([hot_cap][K] floats) or null.
   __device__ __forceinline__ void load(const EpochArgs &p, int64_t tile_base, int lane, bool need_x,
                                        const float *rep = nullptr) {
-    const int g = lane >> 2, t = lane & 3;
-    m[0] = tile_base + g;
-    m[1] = tile_base + g + 8;
-    valid[0] = m[0] < p.end;
-    valid[1] = m[1] < p.end;
+    TileCoords<N> tc;
+    tc.load(p, tile_base, lane, need_x);
+    gather(p, tc, lane, rep);
+  }
+
+  // Decode the coordinates (bounds, cache slots) and gather the rows.
+  __device__ __forceinline__ void gather(const EpochArgs &p, const TileCoords<N> &tc, int lane,
+                                         const float *rep = nullptr) {
+    const int t = lane & 3;
     hot = 0u;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      m[h] = tc.m[h];
+      valid[h] = tc.valid[h];
+      x[h] = tc.x[h];
+    }
 #pragma unroll
     for (int n = 0; n < N; ++n)
 #pragma unroll
-      for (int h = 0; h < 2; ++h) row[n][h] = valid[h] ? __ldcs(p.idx[n] + m[h]) : 0;
+      for (int h = 0; h < 2; ++h) row[n][h] = tc.row[n][h];
     // a coordinate outside [0, I_n) (or a slot outside the cache) masks its
     // nonzero and latches an error
     bool bad = false;
@@ -358,7 +391,8 @@ struct Front {
     }
     if (bad) atomicOr(p.err, ERRBIT_INDEX);
 #pragma unroll
-    for (int h = 0; h < 2; ++h) x[h] = (need_x && valid[h]) ? __ldcs(p.vals + m[h]) : 0.f;
+    for (int h = 0; h < 2; ++h)
+      if (!valid[h]) x[h] = 0.f;
 #pragma unroll
     for (int n = 0; n < N; ++n)
 #pragma unroll
@@ -482,12 +516,12 @@ __device__ void cache_write_back(const EpochArgs &p, const float *rep, unsigned 
 // per-nonzero step e P - lam a is written for the deterministic reduction.
 template <int N, int K, int MATH, bool DELTA>
 __device__ __forceinline__ void factor_tile(const EpochArgs &p, const float *tabs, float *rep,
-                                            unsigned char *dirty, int64_t tile, int lane) {
+                                            unsigned char *dirty, const TileCoords<N> &tc, int lane) {
   constexpr int CPL = K / 4;
   constexpr int TW = Prod<K, MATH>::WORDS;
   const int t = lane & 3;
   Front<N, K, MATH, false> f;
-  f.load(p, p.begin + tile * FT_TILE, lane, true, rep);
+  f.gather(p, tc, lane, rep);
   f.compute(tabs, TW, lane);
   float e[2];
   e[0] = f.x[0] - f.xhat[0];
@@ -568,30 +602,43 @@ __global__ void __launch_bounds__(256) k_factor(const EpochArgs p) {
   const int lane = threadIdx.x & 31;
   const int wpc = blockDim.x >> 5;
   const int64_t ntiles = (p.end - p.begin + FT_TILE - 1) / FT_TILE;
+  // Each warp loads the coordinates and values of its next tile before it
+  // works on the current one, so the stream's DRAM latency overlaps compute.
   if (!cache) {
     const int64_t warp = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = (int64_t(gridDim.x) * blockDim.x) >> 5;
-    for (int64_t tile = warp; tile < ntiles; tile += nwarps)
-      factor_tile<N, K, MATH, DELTA>(p, smem, nullptr, nullptr, tile, lane);
+    TileCoords<N> cur, nxt;
+    if (warp < ntiles) cur.load(p, p.begin + warp * FT_TILE, lane, true);
+    for (int64_t tile = warp; tile < ntiles; tile += nwarps) {
+      const int64_t next = tile + nwarps;
+      if (next < ntiles) nxt.load(p, p.begin + next * FT_TILE, lane, true);
+      factor_tile<N, K, MATH, DELTA>(p, smem, nullptr, nullptr, cur, lane);
+      cur = nxt;
+    }
     return;
   }
   // CTA tile c = warp tiles [c * wpc, c * wpc + wpc); CTA b takes c = b, b + G, ...
   const int64_t nct = (ntiles + wpc - 1) / wpc;
   const int64_t G = gridDim.x;
   const int W = p.hot_window > 0 ? p.hot_window : 1;
-  for (int64_t c0 = blockIdx.x; c0 < nct; c0 += G * W) {
-    for (int k = 0; k < W; ++k) {
-      const int64_t c = c0 + k * G;
-      if (c >= nct) break;
-      const int64_t tile = c * wpc + (threadIdx.x >> 5);
-      if (tile < ntiles) factor_tile<N, K, MATH, false>(p, smem, rep, dirty, tile, lane);
-    }
-    __syncthreads();
-    cache_write_back<N, K>(p, rep, dirty);
-    if (c0 + G * W < nct) {
+  const int wid = threadIdx.x >> 5;
+  TileCoords<N> cur, nxt;
+  if (blockIdx.x < nct) cur.load(p, p.begin + (int64_t(blockIdx.x) * wpc + wid) * FT_TILE, lane, true);
+  int k = 0;
+  for (int64_t c = blockIdx.x; c < nct; c += G) {
+    const int64_t cn = c + G;
+    if (cn < nct) nxt.load(p, p.begin + (cn * wpc + wid) * FT_TILE, lane, true);
+    if (c * wpc + wid < ntiles) factor_tile<N, K, MATH, false>(p, smem, rep, dirty, cur, lane);
+    cur = nxt;
+    if (++k == W || cn >= nct) {
+      k = 0;
       __syncthreads();
-      cache_refresh<N, K>(p, rep);
-      __syncthreads();
+      cache_write_back<N, K>(p, rep, dirty);
+      if (cn < nct) {
+        __syncthreads();
+        cache_refresh<N, K>(p, rep);
+        __syncthreads();
+      }
     }
   }
 }
@@ -740,6 +787,223 @@ __global__ void __launch_bounds__(256) k_core(const EpochArgs p) {
     const size_t o = (size_t(n) * K + j) * K + r;
     out[2 * o] = s;
     out[2 * o + 1] = c;
+  }
+}
+
+// ------------------------------------------- core phase, BF16 in registers
+// The same core-gradient pass (Algorithm 5) for K = 16 with BF16 tensor
+// cores, arranged so that nothing is staged through shared memory:
+//   * C^T = B^T A_Psi^T (mma m16n8k16, M = r, N = the tile's 16 nonzeros,
+//     K = j): the gathered rows, packed to bf16, are already the B operand,
+//     and the accumulator (rows r = g, g + 8; columns m = 2t, 2t + 1 of each
+//     8-nonzero n-tile) is the A-operand layout of the next product;
+//   * D^T = *_{k != n} C^(k)T elementwise; xhat_m by a reduction over r
+//     (3 xor-shuffles over g);
+//   * G^T = D^T E (M = r, N = j, K = the 16 nonzeros): E = (xhat - x) * A_Psi
+//     in the B-operand layout comes from the packed rows by movmatrix.trans
+//     (an 8 x 8 transpose of 16-bit fragments), scaled per nonzero;
+//   * the tile's G^T is added into Neumaier (sum, compensation) registers.
+// Logical contraction index k of the first product maps to the physical
+// column chunk the lane gathered: k = 2t, 2t + 1, 2t + 8, 2t + 9 are
+// columns 4t .. 4t + 3.
+__device__ __forceinline__ int phys_col16(int k) { return 4 * ((k & 7) >> 1) + 2 * (k >> 3) + (k & 1); }
+
+__device__ __forceinline__ uint32_t movmatrix_trans(uint32_t x) {
+  uint32_t y;
+  asm volatile("movmatrix.sync.aligned.m8n8.trans.b16 %0, %1;\n" : "=r"(y) : "r"(x));
+  return y;
+}
+
+__device__ __forceinline__ uint32_t scale_bf16x2(uint32_t v, float s0, float s1) {
+  __nv_bfloat162 h = *reinterpret_cast<__nv_bfloat162 *>(&v);
+  const float2 f = __bfloat1622float2(h);
+  return pack_bf16(f.x * s0, f.y * s1);
+}
+
+template <int N>
+struct CoreRegSmem {
+  static constexpr int TABW = 4 * 32;                  // A-operand words (B^T) per mode
+  static constexpr int ACC = 2 * 8 * 32;               // (sum, comp) x 8 values x 32 lanes per mode
+  static constexpr size_t bytes() { return sizeof(uint32_t) * (size_t(N) * TABW) + sizeof(float) * N * ACC; }
+};
+
+template <int N>
+__global__ void __launch_bounds__(256) k_core_bf16r(const EpochArgs p) {
+  extern __shared__ __align__(16) float smem[];
+  uint32_t *tab = reinterpret_cast<uint32_t *>(smem);      // [N][4][32]
+  float *cacc = smem + N * CoreRegSmem<N>::TABW;            // [N][2][8][32]
+  // B^T as the A operand: reg q of lane (g, t) holds rows r = g + 8 (q & 1),
+  // logical k = 2t + 8 (q >> 1) + {0, 1}
+  for (int e = threadIdx.x; e < N * 128; e += blockDim.x) {
+    const int n = e >> 7, q = (e >> 5) & 3, lane = e & 31;
+    const int g = lane >> 2, t = lane & 3;
+    const int r = g + 8 * (q & 1);
+    const int k0 = 2 * t + 8 * (q >> 1);
+    const int j0 = phys_col16(k0), j1 = phys_col16(k0 + 1);
+    const float v0 = (j0 < p.J[n] && r < p.R) ? p.B[n][j0 * p.R + r] : 0.f;
+    const float v1 = (j1 < p.J[n] && r < p.R) ? p.B[n][j1 * p.R + r] : 0.f;
+    tab[e] = pack_bf16(v0, v1);
+  }
+  for (int e = threadIdx.x; e < N * CoreRegSmem<N>::ACC; e += blockDim.x) cacc[e] = 0.f;
+  __syncthreads();
+
+  const int lane = threadIdx.x & 31;
+  const int g = lane >> 2, t = lane & 3;
+  float gs[N][8], gc[N][8];
+#pragma unroll
+  for (int n = 0; n < N; ++n)
+#pragma unroll
+    for (int i = 0; i < 8; ++i) gs[n][i] = gc[n][i] = 0.f;
+
+  const int64_t warp = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = (int64_t(gridDim.x) * blockDim.x) >> 5;
+  const int64_t ntiles = (p.end - p.begin + FT_TILE - 1) / FT_TILE;
+  // coordinates of rows m = base + g (u = 0) and base + 8 + g (u = 1), and the
+  // values of the lane's columns m = base + 8u + 2t + q, loaded a tile ahead
+  int32_t nrow[N][2];
+  float nxv[2][2];
+  auto load_coords = [&](int64_t tile) {
+    const int64_t b = p.begin + tile * FT_TILE;
+#pragma unroll
+    for (int u = 0; u < 2; ++u)
+#pragma unroll
+      for (int n = 0; n < N; ++n) nrow[n][u] = (b + 8 * u + g < p.end) ? __ldcs(p.idx[n] + b + 8 * u + g) : 0;
+#pragma unroll
+    for (int u = 0; u < 2; ++u)
+#pragma unroll
+      for (int q = 0; q < 2; ++q) {
+        const int64_t m = b + 8 * u + 2 * t + q;
+        nxv[u][q] = m < p.end ? __ldcs(p.vals + m) : 0.f;
+      }
+  };
+  if (warp < ntiles) load_coords(warp);
+  for (int64_t tile = warp; tile < ntiles; tile += nwarps) {
+    const int64_t base = p.begin + tile * FT_TILE;
+    int32_t row[N][2];
+    float xv[2][2];
+    bool valid[2];
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      valid[u] = base + 8 * u + g < p.end;
+#pragma unroll
+      for (int n = 0; n < N; ++n) row[n][u] = nrow[n][u];
+#pragma unroll
+      for (int q = 0; q < 2; ++q) xv[u][q] = nxv[u][q];
+    }
+    if (tile + nwarps < ntiles) load_coords(tile + nwarps);
+    bool bad = false;
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      bool ok = true;
+#pragma unroll
+      for (int n = 0; n < N; ++n) ok = ok && row[n][u] >= 0 && int64_t(row[n][u]) < p.I[n];
+      if (valid[u] && !ok) { bad = true; valid[u] = false; }
+    }
+    if (bad) atomicOr(p.err, ERRBIT_INDEX);
+    // the rows, packed to bf16
+    uint32_t ab[N][2][2];
+#pragma unroll
+    for (int n = 0; n < N; ++n)
+#pragma unroll
+      for (int u = 0; u < 2; ++u) {
+        float v[4];
+        load_chunk<16, true>(p.A[n], row[n][u], p.J[n], t, valid[u], (p.vecmask >> n) & 1, v);
+        ab[n][u][0] = pack_bf16(v[0], v[1]);
+        ab[n][u][1] = pack_bf16(v[2], v[3]);
+      }
+    // C^T per mode: ct[n][u][i], rows r = g + 8 (i >> 1), column m = 8u + 2t + (i & 1)
+    float ct[N][2][4];
+#pragma unroll
+    for (int n = 0; n < N; ++n) {
+      const uint32_t a0 = tab[(n * 4 + 0) * 32 + lane], a1 = tab[(n * 4 + 1) * 32 + lane];
+      const uint32_t a2 = tab[(n * 4 + 2) * 32 + lane], a3 = tab[(n * 4 + 3) * 32 + lane];
+#pragma unroll
+      for (int u = 0; u < 2; ++u) {
+        float acc[4] = {0.f, 0.f, 0.f, 0.f};
+        mma_bf16(acc, a0, a1, a2, a3, ab[n][u][0], ab[n][u][1]);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) ct[n][u][i] = acc[i];
+      }
+    }
+    // xhat of the lane's nonzeros m = 8u + 2t + q, then (xhat - x)
+    float ne[2][2];
+#pragma unroll
+    for (int u = 0; u < 2; ++u)
+#pragma unroll
+      for (int q = 0; q < 2; ++q) {
+        float s0 = 1.f, s1 = 1.f;
+#pragma unroll
+        for (int n = 0; n < N; ++n) { s0 *= ct[n][u][q]; s1 *= ct[n][u][q + 2]; }
+        float sum = s0 + s1;
+        sum += __shfl_xor_sync(FULL, sum, 4);
+        sum += __shfl_xor_sync(FULL, sum, 8);
+        sum += __shfl_xor_sync(FULL, sum, 16);
+        const int64_t m = base + 8 * u + 2 * t + q;
+        ne[u][q] = m < p.end ? sum - xv[u][q] : 0.f;
+      }
+    const bool nonfinite = !isfinite(ne[0][0]) || !isfinite(ne[0][1]) || !isfinite(ne[1][0]) || !isfinite(ne[1][1]);
+    if (__any_sync(FULL, nonfinite) && lane == 0) atomicOr(p.err, ERRBIT_NONFINITE);
+#pragma unroll
+    for (int n = 0; n < N; ++n) {
+      // D^T as the A operand (k = the nonzeros)
+      float d[2][4];
+#pragma unroll
+      for (int u = 0; u < 2; ++u)
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          float pr = 1.f;
+#pragma unroll
+          for (int k = 0; k < N; ++k)
+            if (k != n) pr *= ct[k][u][i];
+          d[u][i] = pr;
+        }
+      const uint32_t da0 = pack_bf16(d[0][0], d[0][1]), da1 = pack_bf16(d[0][2], d[0][3]);
+      const uint32_t da2 = pack_bf16(d[1][0], d[1][1]), da3 = pack_bf16(d[1][2], d[1][3]);
+#pragma unroll
+      for (int v = 0; v < 2; ++v) {
+        // E (k = nonzeros, n = logical j = 8v + g)
+        const uint32_t e0 = scale_bf16x2(movmatrix_trans(ab[n][0][v]), ne[0][0], ne[0][1]);
+        const uint32_t e1 = scale_bf16x2(movmatrix_trans(ab[n][1][v]), ne[1][0], ne[1][1]);
+        float acc[4] = {0.f, 0.f, 0.f, 0.f};
+        mma_bf16(acc, da0, da1, da2, da3, e0, e1);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) neumaier_add(gs[n][4 * v + i], gc[n][4 * v + i], acc[i]);
+      }
+    }
+  }
+  // CTA combine in warp order, then the CTA partial in the [n][K][K] layout
+  const int w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int ww = 0; ww < nw; ++ww) {
+    if (w == ww) {
+#pragma unroll
+      for (int n = 0; n < N; ++n)
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+          float *cs = cacc + ((n * 2 + 0) * 8 + i) * 32 + lane;
+          float *cc = cacc + ((n * 2 + 1) * 8 + i) * 32 + lane;
+          float s = *cs, c = *cc;
+          neumaier_add(s, c, gs[n][i]);
+          *cs = s;
+          *cc = c + gc[n][i];
+        }
+    }
+    __syncthreads();
+  }
+  float *out = p.partial + size_t(blockIdx.x) * 2 * N * 16 * 16;
+  for (int e = threadIdx.x; e < N * 16 * 16; e += blockDim.x) {
+    out[2 * e] = 0.f;
+    out[2 * e + 1] = 0.f;
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < N * 8 * 32; e += blockDim.x) {
+    const int n = e / 256, i = (e >> 5) & 7, ln = e & 31;
+    const int gg = ln >> 2, tt = ln & 3;
+    const int v = i >> 2, ii = i & 3;
+    const int r = gg + 8 * (ii >> 1);
+    const int j = phys_col16(8 * v + 2 * tt + (ii & 1));
+    const size_t o = (size_t(n) * 16 + j) * 16 + r;
+    out[2 * o] = cacc[((n * 2 + 0) * 8 + i) * 32 + ln];
+    out[2 * o + 1] = cacc[((n * 2 + 1) * 8 + i) * 32 + ln];
   }
 }
 

@@ -24,6 +24,14 @@ ft::KernelSet make_set() {
   s.factor_smem = ft::FactorSmem<N, FT_K, FT_MATH>::tables();
   s.core_smem = ft::CoreSmem<N, FT_K, FT_MATH>::bytes();
   s.core_threads = 32 * ft::CoreSmem<N, FT_K, FT_MATH>::WARPS;
+#if FT_K == 16 && FT_MATH == 2
+  // BF16 at K = 16: the register-resident core pass (no shared-memory staging)
+  if constexpr (N <= 4) {
+    s.core = reinterpret_cast<const void *>(&ft::k_core_bf16r<N>);
+    s.core_smem = ft::CoreRegSmem<N>::bytes();
+    s.core_threads = 256;
+  }
+#endif
   return s;
 }
 }  // namespace
