@@ -173,7 +173,70 @@ def make_workload(device, nnz=None, name=WORKLOAD):
     return w, train_idx, train_x, test_idx, test_x, A, B
 
 
+BATCHED = "batched_64"
+
+
+def run_batched(args, rank, world, local_rank):
+    """64 independent tensors (N in {3,4,5}, nnz log-uniform in [1e4, 1e6],
+    I_n log-uniform in [1e3, 1e5], J in {4,8,16}, R in {8,16,32}, planted
+    model + N(0, 0.1) noise) trained by the batched persistent epoch: one
+    captured graph per epoch, launch shapes from the autotuner."""
+    dev = torch.device(f"cuda:{local_rank}")
+    torch.cuda.set_device(dev)
+    ft.load()
+    recipes = synth.batched_recipe(64, seed=0)
+    train, test = [], []
+    for w in recipes:
+        d = synth.draw_workload(w, device=dev)
+        allidx = [d.idx[n].contiguous() for n in range(w.N)]
+        zeros = torch.zeros(d.idx.shape[1], dtype=torch.float32, device=dev)
+        pm = ft.FastTuckerPlus(allidx, zeros, [a.contiguous() for a in d.planted_A],
+                               [b.contiguous() for b in d.planted_B], hot_rows=0)
+        vals = pm.predict(allidx) + d.noise
+        pm.close()
+        A, B = synth.initial_factors(w, device=dev)
+        train.append(([d.idx[n, d.train].contiguous() for n in range(w.N)], vals[d.train].contiguous(), A, B))
+        test.append(([d.idx[n, d.test].contiguous() for n in range(w.N)], vals[d.test].contiguous()))
+    nnz_train = sum(int(t[1].numel()) for t in train)
+    stream = torch.cuda.current_stream(dev)
+    b = ft.FastTuckerBatch(train, precision=args.precision, tune=True)
+    for _ in range(args.warmup):
+        b.epoch(LR, LAM)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    l0 = b.launches
+    with ClockSampler(local_rank) as clk:
+        t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        for _ in range(args.steps):
+            b.epoch(LR, LAM)
+        t1.record(stream)
+        torch.cuda.synchronize()
+    total_ms = t0.elapsed_time(t1)
+    launches = b.launches - l0
+    rm = [b.rmse(k, i, v)[0] for k, (i, v) in enumerate(test)]
+    (total_ms,), value = aggregate_replicas([total_ms], nnz_train, args.steps, world, dev)
+    if rank != 0:
+        return None
+    return {
+        "metric": METRIC + " (batched: 64 tensors, one graph per epoch)", "value": value, "unit": UNIT,
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": {"fp32": "f32", "tf32": "tf32", "bf16": "bf16"}[args.precision],
+        "data": "synthetic (64 planted tensors of uneven order, size and rank, uniform coordinates)",
+        "config": {"workload": BATCHED, "tensors": 64, "nnz_train": nnz_train, "precision": args.precision,
+                   "classes": b.classes(), "lr": LR, "lambda": LAM,
+                   "l2": "inputs larger than L2 (training COO 216 MB per epoch)"},
+        "mean_test_rmse": sum(rm) / len(rm),
+        "gpu_launches": int(launches),
+        "clocks": clk.summary(),
+    }
+
+
 def run_ours(args, rank, world, local_rank):
+    if args.workload == BATCHED:
+        return run_batched(args, rank, world, local_rank)
     dev = torch.device(f"cuda:{local_rank}")
     torch.cuda.set_device(dev)
     ft.load()
@@ -290,9 +353,55 @@ def run_ours(args, rank, world, local_rank):
         "gpu_launches": int(launches),
         "clocks": clocks,
     }
+    if not args.no_time_to_rmse:
+        out["time_to_rmse"] = time_to_rmse(w, tri, trx, tei, tex, dev, args.ttr_epochs, args.precision)
     if not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(args.cpu_sample)
     return out
+
+
+def time_to_rmse(w, tri, trx, tei, tex, dev, epochs, precision):
+    """Wall time for the mixed-precision run to reach the test RMSE that plain
+    FP32 (CUDA cores) reaches after `epochs` epochs, both from the same start.
+    An epoch is factor phase + core phase + test RMSE; times are CUDA events."""
+    A0, B0 = synth.initial_factors(w, device=dev, mean_value=float(trx.double().mean()))
+
+    def run(prec, max_epochs, target=None):
+        A = [a.clone() for a in A0]
+        B = [b.clone() for b in B0]
+        m = ft.FastTuckerPlus(tri, trx, A, B, precision=prec)
+        stream = torch.cuda.current_stream(dev)
+        torch.cuda.synchronize()
+        t0 = torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        curve, times = [], []
+        for ep in range(max_epochs):
+            m.epoch_factors(LR, LAM)
+            m.epoch_core(LR, LAM)
+            r = m.rmse(tei, tex)[0]
+            t1 = torch.cuda.Event(enable_timing=True)
+            t1.record(stream)
+            t1.synchronize()
+            curve.append(r)
+            times.append(t0.elapsed_time(t1) / 1e3)
+            if target is not None and r <= target:
+                break
+        m.close()
+        return curve, times
+
+    base_curve, base_times = run("fp32", epochs)
+    target = base_curve[-1]
+    fast_curve, fast_times = run(precision, 3 * epochs, target)
+    reached = fast_curve[-1] <= target
+    return {
+        "target_test_rmse": target, "baseline": "fp32", "candidate": precision,
+        "baseline_epochs": len(base_curve), "baseline_seconds": base_times[-1],
+        "candidate_epochs": len(fast_curve), "candidate_seconds": fast_times[-1] if reached else None,
+        "reached": reached,
+        "speedup": (base_times[-1] / fast_times[-1]) if reached else None,
+        "baseline_curve": [round(v, 5) for v in base_curve],
+        "candidate_curve": [round(v, 5) for v in fast_curve],
+    }
 
 
 def oracle_sample(nnz_sample):
@@ -368,10 +477,13 @@ def main():
     ap.add_argument("--cpu-sample", type=int, default=2_000_000)
     ap.add_argument("--ref-sample", type=int, default=1_000_000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-time-to-rmse", action="store_true")
+    ap.add_argument("--ttr-epochs", type=int, default=10,
+                    help="epochs of the plain FP32 run that sets the time-to-RMSE target")
     ap.add_argument("--hot-rows", type=int, default=None,
                     help="rows per mode in the shared-memory hot-row cache (-1 auto, 0 off)")
     ap.add_argument("--hot-window", type=int, default=None, help="CTA tiles between cache write-backs")
-    ap.add_argument("--workload", default=WORKLOAD, choices=sorted(synth.WORKLOADS),
+    ap.add_argument("--workload", default=WORKLOAD, choices=sorted(synth.WORKLOADS) + [BATCHED],
                     help="the timed tensor (default: the Netflix-shaped 1e8 Zipf tensor)")
     ap.add_argument("--nnz", type=int, default=None,
                     help="distinct coordinates drawn (default: the workload's 1e8); "

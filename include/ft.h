@@ -29,8 +29,8 @@
  *     J_n x R.  Both are caller-owned, borrowed by the context, and updated
  *     in place by the epochs.
  *   - Supported shapes: 1 <= N <= 8, 1 <= J_n <= 32, 1 <= R <= 32, with
- *     N * K <= 128 where K = 16 if max(J_n, R) <= 16, else 32.  Others
- *     return FT_ERR_SHAPE.  nnz < 2^31.
+ *     N * K <= 160 where K = 16 if max(J_n, R) <= 16, else 32 (so N <= 8 at
+ *     K = 16 and N <= 5 at K = 32).  Others return FT_ERR_SHAPE.  nnz < 2^31.
  *   - The library allocates no device memory: all scratch lives in a
  *     caller-provided workspace (ft_workspace_size), 256-byte aligned.
  *     The context itself is the only (host-heap) allocation.
@@ -170,6 +170,68 @@ ft_status ft_core_grad_noalloc(int N, const int64_t *I, const int *J, int R, int
                                const int32_t *const *idx, const float *vals,
                                const float *const *A, const float *const *B, int precision,
                                float *G_out, void *stream);
+
+/* ---------------------------------------------------------------- batches
+ * Many independent tensors trained together (each with its own order N,
+ * ranks J_n and R, nonzeros and matrices).  Tensors are grouped by kernel
+ * class (N, padded rank K); every class runs one persistent factor kernel and
+ * one persistent core kernel over fixed-size units of its tensors' tiles, and
+ * the whole epoch - the factor pass (Hogwild within each tensor), the core
+ * pass and one finalize over all tensors - is captured once as a CUDA graph
+ * and replayed by ft_batch_epoch.  The paper treats one tensor at a time
+ * (Algorithms 3-5); each tensor of a batch follows exactly those rules.
+ */
+typedef struct {
+  int N;
+  const int64_t *I;           /* host, N mode sizes */
+  const int *J;               /* host, N factor ranks */
+  int R;
+  int64_t nnz;
+  const int32_t *const *idx;  /* host array of N device pointers (nnz int32 each) */
+  const float *vals;          /* device, nnz values */
+  float *const *A;            /* host array of N device pointers, I_n x J_n */
+  float *const *B;            /* host array of N device pointers, J_n x R */
+} ft_tensor_desc;
+
+typedef struct ft_batch ft_batch;
+
+/* Workspace bytes for a batch (host call; queries the current device).
+ * cfg: precision as for ft_init; scatter must be FT_HOGWILD; the hot-row
+ * cache is not used by batches. */
+ft_status ft_batch_workspace_size(int ntensors, const ft_tensor_desc *tensors,
+                                  const ft_config *cfg, size_t *bytes);
+
+/* Validate every tensor (as ft_init does), lay out the units with default
+ * launch shapes and capture the epoch graph.  The descriptors' host arrays
+ * are copied; the device buffers are borrowed.  Synchronises the stream. */
+ft_status ft_batch_init(ft_batch **out, int ntensors, const ft_tensor_desc *tensors,
+                        const ft_config *cfg, void *workspace, size_t ws_bytes, void *stream);
+
+/* Autotuner: for every kernel class, time the core pass (which changes no
+ * factor or core matrix) over candidate launch shapes - tiles per work unit
+ * and CTAs per SM - keep the fastest, and recapture the epoch graph.
+ * Synchronises the stream. */
+ft_status ft_batch_tune(ft_batch *b, void *stream);
+
+/* One epoch of every tensor: factor pass (Algorithm 4), core pass and
+ * finalize (Algorithm 5), by one replay of the captured graph. */
+ft_status ft_batch_epoch(ft_batch *b, float lr_a, float lambda_a, float lr_b, float lambda_b,
+                         void *stream);
+
+/* Test errors of tensor `tensor` of the batch, as ft_rmse. */
+ft_status ft_batch_rmse(ft_batch *b, int tensor, int64_t n, const int32_t *const *idx,
+                        const float *vals, double *out3, void *stream);
+
+/* Number of kernel classes, and the launch shape of class `cls`:
+ * out6 = {N, K, tensors in the class, warp tiles per unit, CTAs per SM,
+ * units}. */
+int ft_batch_num_classes(const ft_batch *b);
+ft_status ft_batch_class_info(const ft_batch *b, int cls, int64_t *out6);
+
+/* Kernels launched by this batch since ft_batch_init (graph nodes included). */
+int64_t ft_batch_launch_count(const ft_batch *b);
+
+void ft_batch_destroy(ft_batch *b);
 
 /* Predictions xhat (float32) of n coordinates (idx: host array of N device
  * pointers; out: device, n floats) with the context's current A and B. */

@@ -25,10 +25,14 @@ NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompil
               f"-I{INCLUDE}", f"-I{CSRC}"]
 
 # (source, extra defines, object name)
-UNITS = [("ft_api.cu", [], "ft_api")]
+UNITS = [("ft_api.cu", [], "ft_api"), ("ft_batch.cu", [], "ft_batch")]
+# the slowest units first, so a parallel build finishes early
+for _m in (0, 1, 2):
+    for _k in (32, 16):
+        for _n in range(5 if _k == 32 else 8, 0, -1):
+            UNITS.append(("ft_inst.cu", [f"-DFT_K={_k}", f"-DFT_MATH={_m}", f"-DFT_N={_n}"],
+                          f"ft_inst_{_k}_{_m}_{_n}"))
 for _k in (16, 32):
-    for _m in (0, 1, 2):
-        UNITS.append(("ft_inst.cu", [f"-DFT_K={_k}", f"-DFT_MATH={_m}"], f"ft_inst_{_k}_{_m}"))
     UNITS.append(("ft_eval.cu", [f"-DFT_K={_k}"], f"ft_eval_{_k}"))
 
 
@@ -67,7 +71,8 @@ def build(force: bool = False, jobs: int | None = None, verbose: bool = False,
             if f.read().strip() == digest:
                 return lib_path
     exe = nvcc()
-    jobs = jobs or max(1, min(len(UNITS), os.cpu_count() or 1))
+    jobs = jobs or max(1, min(len(UNITS), len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity")
+                                 else (os.cpu_count() or 1)))
 
     def compile_unit(unit):
         src, defs, name = unit

@@ -234,21 +234,13 @@ ft_status make_plan(int N, const int64_t *I, const int *J, int R, int64_t nnz, c
     p->sumJ += J[n];
   }
   const int K = maxr <= 16 ? 16 : 32;
-  if (N * K > 128) return FT_ERR_SHAPE;
+  if (N * K > 160) return FT_ERR_SHAPE;
   p->N = N;
   p->R = R;
   p->K = K;
   p->nnz = nnz;
   p->cfg = c;
-  bool ok = false;
-  switch (K * 10 + c.precision) {
-    case 160: ok = ft_kernels_16_0(N, &p->ks); break;
-    case 161: ok = ft_kernels_16_1(N, &p->ks); break;
-    case 162: ok = ft_kernels_16_2(N, &p->ks); break;
-    case 320: ok = ft_kernels_32_0(N, &p->ks); break;
-    case 321: ok = ft_kernels_32_1(N, &p->ks); break;
-    case 322: ok = ft_kernels_32_2(N, &p->ks); break;
-  }
+  bool ok = ft_kernel_set(N, K, c.precision, &p->ks);
   if (!ok) return FT_ERR_SHAPE;
   ok = K == 16 ? ft_eval_16(N, &p->es) : ft_eval_32(N, &p->es);
   if (!ok) return FT_ERR_SHAPE;

@@ -1060,3 +1060,137 @@ __global__ void __launch_bounds__(256) k_eval(const EpochArgs p) {
 }
 
 }  // namespace ft
+
+// ===================================================== batched persistent epoch
+// Many independent tensors in one launch per kernel class (N, K, precision).
+// The tiles of every tensor of the class are cut into units of a fixed number
+// of CTA tiles; CTA b takes units b, b + G, b + 2G, ...  A CTA reloads the
+// tensor's arguments and operand tables only when its next unit belongs to
+// another tensor.  The factor pass is Hogwild within each tensor; the core
+// pass writes one compensated partial per unit, reduced per tensor in unit
+// order by k_batch_finalize (reproducible bit for bit).
+namespace ft {
+
+struct BatchUnit {
+  int32_t tensor;       // index into the tensor table
+  int32_t pad;
+  int64_t tile_begin;   // warp tiles [tile_begin, tile_end) of that tensor
+  int64_t tile_end;
+  int64_t poff;         // float offset of the unit's core partial (2 * N * K * K floats)
+};
+
+struct BatchArgs {
+  const EpochArgs *tensors;   // per-tensor arguments (device)
+  const BatchUnit *units;     // units of this kernel class
+  int nunits;
+  float *partial;             // core partials
+  const float *hyper;         // lr_a, lambda_a, lr_b, lambda_b (device)
+};
+
+template <int N, int K, int MATH>
+__global__ void __launch_bounds__(256) k_batch_factor(const BatchArgs b) {
+  extern __shared__ __align__(16) float smem[];
+  __shared__ EpochArgs ea;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, wpc = blockDim.x >> 5;
+  int cur = -1;
+  for (int u = blockIdx.x; u < b.nunits; u += gridDim.x) {
+    const BatchUnit un = b.units[u];
+    if (un.tensor != cur) {
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        ea = b.tensors[un.tensor];
+        ea.lr = b.hyper[0];
+        ea.lam = b.hyper[1];
+      }
+      __syncthreads();
+      fill_tables<N, K, MATH>(smem, ea, true);
+      __syncthreads();
+      cur = un.tensor;
+    }
+    for (int64_t tile = un.tile_begin + wid; tile < un.tile_end; tile += wpc) {
+      TileCoords<N> tc;
+      tc.load(ea, ea.begin + tile * FT_TILE, lane, true);
+      factor_tile<N, K, MATH, false>(ea, smem, nullptr, nullptr, tc, lane);
+    }
+  }
+}
+
+template <int N, int K, int MATH>
+__global__ void __launch_bounds__(256) k_batch_core(const BatchArgs b) {
+  extern __shared__ __align__(16) float smem[];
+  __shared__ EpochArgs ea;
+  using L = CoreSmem<N, K, MATH>;
+  constexpr int CPL = K / 4;
+  constexpr int TW = L::TW;
+  constexpr int LD = L::LD;
+  constexpr int SL = GradTile<K, MATH>::SLOTS;
+  const int wid = threadIdx.x >> 5, wpc = blockDim.x >> 5;
+  const int lane = threadIdx.x & 31;
+  const int g = lane >> 2, t = lane & 3;
+  float *stage = smem + N * TW + wid * (L::STAGE + L::ACC);
+  float *Es = stage, *Ds = stage + FT_TILE * LD;
+  float *acc_s = stage + L::STAGE;
+  float *acc_c = acc_s + N * SL * 32;
+  int cur = -1;
+  for (int u = blockIdx.x; u < b.nunits; u += gridDim.x) {
+    const BatchUnit un = b.units[u];
+    __syncthreads();
+    if (un.tensor != cur) {
+      if (threadIdx.x == 0) ea = b.tensors[un.tensor];
+      __syncthreads();
+      fill_tables<N, K, MATH>(smem, ea, false);
+      cur = un.tensor;
+    }
+    for (int q = lane; q < N * SL * 32; q += 32) { acc_s[q] = 0.f; acc_c[q] = 0.f; }
+    __syncthreads();
+    for (int64_t tile = un.tile_begin + wid; tile < un.tile_end; tile += wpc) {
+      Front<N, K, MATH, true> f;
+      f.load(ea, ea.begin + tile * FT_TILE, lane, true);
+      f.compute(smem, TW, lane);
+      const float ne0 = f.xhat[0] - f.x[0], ne1 = f.xhat[1] - f.x[1];
+#pragma unroll
+      for (int n = 0; n < N; ++n) {
+        float d[2][CPL];
+        f.leave_one_out(n, d);
+#pragma unroll
+        for (int q = 0; q < CPL; ++q) {
+          Es[g * LD + CPL * t + q] = ne0 * f.a[n][0][q];
+          Es[(g + 8) * LD + CPL * t + q] = ne1 * f.a[n][1][q];
+          Ds[g * LD + CPL * t + q] = d[0][q];
+          Ds[(g + 8) * LD + CPL * t + q] = d[1][q];
+        }
+        __syncwarp();
+        float part[SL];
+        GradTile<K, MATH>::run(Es, Ds, part, lane);
+        __syncwarp();
+#pragma unroll
+        for (int q = 0; q < SL; ++q) {
+          const int o = (n * SL + q) * 32 + lane;
+          float s = acc_s[o], c = acc_c[o];
+          neumaier_add(s, c, part[q]);
+          acc_s[o] = s;
+          acc_c[o] = c;
+        }
+      }
+    }
+    __syncthreads();
+    float *out = b.partial + un.poff;
+    for (int f = threadIdx.x; f < N * SL * 32; f += blockDim.x) {
+      float s = 0.f, c = 0.f;
+      for (int w = 0; w < wpc; ++w) {
+        const float *ws = smem + N * TW + w * (L::STAGE + L::ACC) + L::STAGE;
+        neumaier_add(s, c, ws[f]);
+        c += ws[N * SL * 32 + f];
+      }
+      const int ln = f & 31, q = (f >> 5) % SL, n = f / (SL * 32);
+      const int gg = ln >> 2, tt = ln & 3;
+      const int i = q & 3, uu = (q >> 2) % (K / 8), mt = (q >> 2) / (K / 8);
+      const int j = 16 * mt + gg + 8 * (i >> 1), r = 8 * uu + 2 * tt + (i & 1);
+      const size_t o = (size_t(n) * K + j) * K + r;
+      out[2 * o] = s;
+      out[2 * o + 1] = c;
+    }
+  }
+}
+
+}  // namespace ft

@@ -27,8 +27,8 @@ bool FT_CAT(ft_eval, FT_K)(int N, ft::EvalSet *out) {
     case 2: *out = make_eval<2>(); return true;
     case 3: *out = make_eval<3>(); return true;
     case 4: *out = make_eval<4>(); return true;
-#if FT_K == 16
     case 5: *out = make_eval<5>(); return true;
+#if FT_K == 16
     case 6: *out = make_eval<6>(); return true;
     case 7: *out = make_eval<7>(); return true;
     case 8: *out = make_eval<8>(); return true;

@@ -1,6 +1,6 @@
-// Explicit instantiations of the epoch kernels for one padded rank K and one
-// precision.  Built once per (FT_K, FT_MATH) pair so the units compile in
-// parallel.
+// Explicit instantiations of the epoch kernels for one padded rank K, one
+// precision and one order N.  Built once per (FT_K, FT_MATH, FT_N) so the
+// units compile in parallel.
 #include "ft_device.cuh"
 #include "ft_internal.h"
 
@@ -11,8 +11,12 @@
 #error "FT_MATH must be defined (0 = FP32, 1 = TF32, 2 = BF16)"
 #endif
 
-#define FT_CAT_(a, b, c) a##_##b##_##c
-#define FT_CAT(a, b, c) FT_CAT_(a, b, c)
+#ifndef FT_N
+#error "FT_N must be defined (the order N of this unit)"
+#endif
+
+#define FT_CAT_(a, b, c, d) a##_##b##_##c##_##d
+#define FT_CAT(a, b, c, d) FT_CAT_(a, b, c, d)
 
 namespace {
 template <int N>
@@ -24,6 +28,10 @@ ft::KernelSet make_set() {
   s.factor_smem = ft::FactorSmem<N, FT_K, FT_MATH>::tables();
   s.core_smem = ft::CoreSmem<N, FT_K, FT_MATH>::bytes();
   s.core_threads = 32 * ft::CoreSmem<N, FT_K, FT_MATH>::WARPS;
+  s.batch_factor = reinterpret_cast<const void *>(&ft::k_batch_factor<N, FT_K, FT_MATH>);
+  s.batch_core = reinterpret_cast<const void *>(&ft::k_batch_core<N, FT_K, FT_MATH>);
+  s.batch_core_smem = ft::CoreSmem<N, FT_K, FT_MATH>::bytes();
+  s.batch_core_threads = 32 * ft::CoreSmem<N, FT_K, FT_MATH>::WARPS;
 #if FT_K == 16 && FT_MATH == 2
   // BF16 at K = 16: the register-resident core pass (no shared-memory staging)
   if constexpr (N <= 4) {
@@ -36,18 +44,7 @@ ft::KernelSet make_set() {
 }
 }  // namespace
 
-bool FT_CAT(ft_kernels, FT_K, FT_MATH)(int N, ft::KernelSet *out) {
-  switch (N) {
-    case 1: *out = make_set<1>(); return true;
-    case 2: *out = make_set<2>(); return true;
-    case 3: *out = make_set<3>(); return true;
-    case 4: *out = make_set<4>(); return true;
-#if FT_K == 16
-    case 5: *out = make_set<5>(); return true;
-    case 6: *out = make_set<6>(); return true;
-    case 7: *out = make_set<7>(); return true;
-    case 8: *out = make_set<8>(); return true;
-#endif
-    default: return false;
-  }
+bool FT_CAT(ft_kernels, FT_K, FT_MATH, FT_N)(ft::KernelSet *out) {
+  *out = make_set<FT_N>();
+  return true;
 }

@@ -14,6 +14,11 @@ struct KernelSet {
   size_t factor_smem = 0;              // tables only; the hot-row cache adds to it
   size_t core_smem = 0;
   int core_threads = 256;
+  // batched persistent kernels of this class (generic core, shared-memory staging)
+  const void *batch_factor = nullptr;
+  const void *batch_core = nullptr;
+  size_t batch_core_smem = 0;
+  int batch_core_threads = 256;
 };
 
 // FP32 prediction / error kernels of one (N, K).
@@ -26,14 +31,24 @@ struct EvalSet {
 }  // namespace ft
 
 // One entry point per compiled instantiation unit (ft_inst.cu built with
-// FT_K in {16, 32} and FT_MATH in {0, 1, 2}; ft_eval.cu built with FT_K).
-#define FT_DECLARE_SET(K, M) bool ft_kernels_##K##_##M(int N, ft::KernelSet *out);
-FT_DECLARE_SET(16, 0)
-FT_DECLARE_SET(16, 1)
-FT_DECLARE_SET(16, 2)
-FT_DECLARE_SET(32, 0)
-FT_DECLARE_SET(32, 1)
-FT_DECLARE_SET(32, 2)
+// FT_K in {16, 32}, FT_MATH in {0, 1, 2} and FT_N in 1..8 at K = 16, 1..5 at
+// K = 32; ft_eval.cu built with FT_K).
+#define FT_SETS_OF(X, K, M) X(K, M, 1) X(K, M, 2) X(K, M, 3) X(K, M, 4) X(K, M, 5)
+#define FT_SETS16(X, M) FT_SETS_OF(X, 16, M) X(16, M, 6) X(16, M, 7) X(16, M, 8)
+#define FT_ALL_SETS(X) \
+  FT_SETS16(X, 0) FT_SETS16(X, 1) FT_SETS16(X, 2) FT_SETS_OF(X, 32, 0) FT_SETS_OF(X, 32, 1) FT_SETS_OF(X, 32, 2)
+#define FT_DECLARE_SET(K, M, N) bool ft_kernels_##K##_##M##_##N(ft::KernelSet *out);
+FT_ALL_SETS(FT_DECLARE_SET)
 #undef FT_DECLARE_SET
+
+// Kernels of one (N, K, precision), false if that combination is not built.
+inline bool ft_kernel_set(int N, int K, int precision, ft::KernelSet *out) {
+#define FT_CASE(KK, MM, NN) \
+  if (K == KK && precision == MM && N == NN) return ft_kernels_##KK##_##MM##_##NN(out);
+  FT_ALL_SETS(FT_CASE)
+#undef FT_CASE
+  return false;
+}
+
 bool ft_eval_16(int N, ft::EvalSet *out);
 bool ft_eval_32(int N, ft::EvalSet *out);

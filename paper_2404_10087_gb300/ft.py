@@ -30,13 +30,22 @@ STATUS = {0: "FT_OK", -1: "FT_ERR_ARG", -2: "FT_ERR_INDEX", -3: "FT_ERR_SHAPE", 
 # Every symbol the header declares (checked by the tests against the library).
 EXPORTS = ["ft_config_default", "ft_workspace_size", "ft_init", "ft_epoch_factors",
            "ft_epoch_core", "ft_core_grad", "ft_predict", "ft_rmse", "ft_check",
-           "ft_launch_count", "ft_destroy", "ft_status_str", "ft_core_grad_noalloc"]
+           "ft_launch_count", "ft_destroy", "ft_status_str", "ft_core_grad_noalloc",
+           "ft_batch_workspace_size", "ft_batch_init", "ft_batch_tune", "ft_batch_epoch",
+           "ft_batch_rmse", "ft_batch_num_classes", "ft_batch_class_info", "ft_batch_launch_count",
+           "ft_batch_destroy"]
 
 
 class FtError(RuntimeError):
     def __init__(self, status: int, where: str):
         self.status = status
         super().__init__(f"{where}: {STATUS.get(status, status)}")
+
+
+class ft_tensor_desc(ctypes.Structure):
+    _fields_ = [("N", ctypes.c_int), ("I", ctypes.c_void_p), ("J", ctypes.c_void_p), ("R", ctypes.c_int),
+                ("nnz", ctypes.c_int64), ("idx", ctypes.c_void_p), ("vals", ctypes.c_void_p),
+                ("A", ctypes.c_void_p), ("B", ctypes.c_void_p)]
 
 
 class ft_config(ctypes.Structure):
@@ -88,6 +97,15 @@ def _declare(lib):
         "ft_destroy": (None, [_P]),
         "ft_status_str": (ctypes.c_char_p, [INT]),
         "ft_core_grad_noalloc": (INT, [INT, _P, _P, INT, I64, _P, _P, _P, _P, INT, _P, _P]),
+        "ft_batch_workspace_size": (INT, [INT, _P, _P, _P]),
+        "ft_batch_init": (INT, [_P, INT, _P, _P, _P, ctypes.c_size_t, _P]),
+        "ft_batch_tune": (INT, [_P, _P]),
+        "ft_batch_epoch": (INT, [_P, FLT, FLT, FLT, FLT, _P]),
+        "ft_batch_rmse": (INT, [_P, INT, I64, _P, _P, _P, _P]),
+        "ft_batch_num_classes": (INT, [_P]),
+        "ft_batch_class_info": (INT, [_P, INT, _P]),
+        "ft_batch_launch_count": (I64, [_P]),
+        "ft_batch_destroy": (None, [_P]),
     }
     for name, (res, args) in sigs.items():
         f = getattr(lib, name)
@@ -279,6 +297,121 @@ class FastTuckerPlus:
         if getattr(self, "ctx", None):
             ft_destroy(self.ctx)
             self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# --------------------------------------------------------------- batches
+class _Descs:
+    """ft_tensor_desc array plus the host arrays it points to."""
+
+    def __init__(self, tensors):
+        self.keep = []
+        self.arr = (ft_tensor_desc * len(tensors))()
+        for d, (idx, vals, A, B) in zip(self.arr, tensors):
+            N = len(A)
+            I = (ctypes.c_int64 * N)(*[int(a.shape[0]) for a in A])
+            J = (ctypes.c_int * N)(*[int(a.shape[1]) for a in A])
+            pi, pa, pb = _ptrs(idx), _ptrs(A), _ptrs(B)
+            self.keep += [I, J, pi, pa, pb]
+            d.N, d.R, d.nnz = N, int(B[0].shape[1]), int(vals.numel())
+            d.I, d.J = ctypes.addressof(I), ctypes.addressof(J)
+            d.idx, d.A, d.B = ctypes.addressof(pi), ctypes.addressof(pa), ctypes.addressof(pb)
+            d.vals = vals.data_ptr() if vals.numel() else 0
+
+
+def ft_batch_workspace_size(tensors, cfg: ft_config) -> int:
+    ds = _Descs(tensors)
+    out = ctypes.c_size_t(0)
+    _check(load().ft_batch_workspace_size(len(tensors), ds.arr, ctypes.byref(cfg), ctypes.byref(out)),
+           "ft_batch_workspace_size")
+    return int(out.value)
+
+
+def ft_batch_init(tensors, workspace, cfg: ft_config, stream=None):
+    ds = _Descs(tensors)
+    h = ctypes.c_void_p(0)
+    _check(load().ft_batch_init(ctypes.byref(h), len(tensors), ds.arr, ctypes.byref(cfg),
+                                workspace.data_ptr(), workspace.numel(), _stream(stream)), "ft_batch_init")
+    return h.value
+
+
+def ft_batch_tune(b, stream=None):
+    _check(load().ft_batch_tune(b, _stream(stream)), "ft_batch_tune")
+
+
+def ft_batch_epoch(b, lr_a, lambda_a, lr_b, lambda_b, stream=None):
+    _check(load().ft_batch_epoch(b, float(lr_a), float(lambda_a), float(lr_b), float(lambda_b),
+                                 _stream(stream)), "ft_batch_epoch")
+
+
+def ft_batch_rmse(b, tensor, idx, vals, stream=None):
+    n = int(vals.numel())
+    out = (ctypes.c_double * 3)()
+    _check(load().ft_batch_rmse(b, int(tensor), n, _ptrs(idx) if n else None,
+                                vals.data_ptr() if n else None, out, _stream(stream)), "ft_batch_rmse")
+    return float(out[0]), float(out[1]), float(out[2])
+
+
+def ft_batch_num_classes(b) -> int:
+    return int(load().ft_batch_num_classes(b))
+
+
+def ft_batch_class_info(b, cls):
+    out = (ctypes.c_int64 * 6)()
+    _check(load().ft_batch_class_info(b, int(cls), out), "ft_batch_class_info")
+    keys = ("N", "K", "tensors", "unit_tiles", "ctas_per_sm", "units")
+    return dict(zip(keys, [int(v) for v in out]))
+
+
+def ft_batch_launch_count(b) -> int:
+    return int(load().ft_batch_launch_count(b))
+
+
+def ft_batch_destroy(b):
+    if b:
+        load().ft_batch_destroy(b)
+
+
+class FastTuckerBatch:
+    """Independent tensors trained together.  tensors: list of
+    (idx list, vals, A list, B list) device tensors, as for FastTuckerPlus."""
+
+    def __init__(self, tensors, precision="fp32", stream=None, tune=False):
+        self.tensors = [(list(i), v, list(a), list(b)) for i, v, a, b in tensors]
+        self.cfg = make_config(precision, "hogwild")
+        ws = ft_batch_workspace_size(self.tensors, self.cfg)
+        dev = self.tensors[0][1].device
+        self.workspace = torch.empty(max(ws, 256), dtype=torch.uint8, device=dev)
+        self.handle = ft_batch_init(self.tensors, self.workspace, self.cfg, stream)
+        if tune:
+            self.tune(stream)
+
+    def tune(self, stream=None):
+        ft_batch_tune(self.handle, stream)
+
+    def epoch(self, lr_a, lam_a, lr_b=None, lam_b=None, stream=None):
+        ft_batch_epoch(self.handle, lr_a, lam_a, lr_a if lr_b is None else lr_b,
+                       lam_a if lam_b is None else lam_b, stream)
+
+    def rmse(self, tensor, idx, vals, stream=None):
+        return ft_batch_rmse(self.handle, tensor, idx, vals, stream)
+
+    def classes(self):
+        return [ft_batch_class_info(self.handle, c) for c in range(ft_batch_num_classes(self.handle))]
+
+    @property
+    def launches(self) -> int:
+        return ft_batch_launch_count(self.handle)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            ft_batch_destroy(self.handle)
+            self.handle = None
 
     def __del__(self):
         try:

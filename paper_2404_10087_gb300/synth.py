@@ -254,3 +254,23 @@ def random_problem(seed: int, I, J, R, nnz, device="cpu", std=None, value_std=1.
     B = [normal_matrices(gen, [(Jn, R)], s, device)[0] for Jn, s in zip(J, sd)]
     x = (torch.randn(nnz, generator=gen, device=device, dtype=torch.float64) * value_std).to(torch.float32)
     return idx, x, A, B
+
+
+# ------------------------------------------------------------ batches
+def batched_recipe(count: int = 64, seed: int = 0):
+    """Shapes of a batch of independent tensors of uneven order and size:
+    N uniform in {3, 4, 5}, nnz log-uniform in [1e4, 1e6], every I_n
+    log-uniform in [1e3, 1e5], J_n uniform in {4, 8, 16} (one J per tensor),
+    R uniform in {8, 16, 32}."""
+    gen = generator(seed)
+    out = []
+    for k in range(count):
+        u = torch.rand(4 + 5, generator=gen, dtype=torch.float64)
+        N = 3 + int(u[0] * 3)
+        nnz = int(round(10 ** (4 + 2 * float(u[1]))))
+        J = (4, 8, 16)[int(u[2] * 3)]
+        R = (8, 16, 32)[int(u[3] * 3)]
+        I = tuple(int(round(10 ** (3 + 2 * float(u[4 + n])))) for n in range(N))
+        out.append(Workload(name=f"batch{count}_{k}", I=I, nnz=nnz, J=(J,) * N, R=R, dist="uniform",
+                            noise_std=0.1, seed=seed * 1000 + k + 1))
+    return out

@@ -55,7 +55,7 @@ def test_shape_rejection_before_any_device_call():
     for I, J, R in [((10,) * 9, (4,) * 9, 4),       # N > 8
                     ((10, 10), (4, 33), 4),          # J > 32
                     ((10, 10), (4, 4), 33),          # R > 32
-                    ((10,) * 5, (32,) * 5, 8),       # N * K > 128
+                    ((10,) * 6, (32,) * 6, 8),       # N * K > 160
                     ((10, 10), (0, 4), 4)]:          # J < 1
         with pytest.raises(ft.FtError) as e:
             ft.ft_workspace_size(I, J, R, 100, cfg)
