@@ -92,6 +92,10 @@ def _declare(lib):
         "orc_core_epoch": [_INT, _P, _INT, _P, _P, _I64, _P, _P, _DBL, _DBL, _INT],
         "orc_errors": [_INT, _P, _INT, _P, _P, _I64, _P, _P, _P, _INT],
         "orc_objective": [_INT, _P, _P, _INT, _P, _P, _I64, _P, _P, _DBL, _DBL, _P, _INT],
+        "orc_row_stats": [_INT, _P, _P, _INT, _P, _P, _I64, _P, _P, _DBL, _DBL, _DBL, _P, _P, _P],
+        "orc_mlp_nparams": [],
+        "orc_mlp_forward": [_P, _I64, _P, _P],
+        "orc_mlp_grad": [_P, _I64, _P, _P, _P, _P],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -244,3 +248,44 @@ def objective(A, B, idx, x, lam_a: float, lam_b: float, nthreads: int = 1) -> fl
                                 _ptr(xv), float(lam_a), float(lam_b), _ptr(out), nthreads),
            "orc_objective")
     return float(out[0])
+
+
+# ------------------------------------------------------ learned step sizes
+def row_stats(A, B, idx, x, lam: float, gamma: float, beta: float = 0.0, ema_in=None, labels=True):
+    """(features [rows, 3], labels [rows] or None), rows of all modes
+    concatenated; see orc_row_stats in ft_oracle.c for the definitions."""
+    m = _Model(A, B)
+    cols, pidx, nnz = _coords(idx, m.N)
+    xv = np.ascontiguousarray(x, dtype=np.float64)
+    rows = int(m.I.sum())
+    feat = np.empty((rows, 3))
+    lab = np.empty(rows) if labels else None
+    ema = None if ema_in is None else np.ascontiguousarray(ema_in, dtype=np.float64)
+    _check(load().orc_row_stats(m.N, _ptr(m.I), _ptr(m.J), m.R, m.pA, m.pB, nnz, pidx, _ptr(xv),
+                                float(lam), float(gamma), float(beta),
+                                None if ema is None else _ptr(ema), _ptr(feat),
+                                None if lab is None else _ptr(lab)), "orc_row_stats")
+    return feat, lab
+
+
+def mlp_nparams() -> int:
+    return int(load().orc_mlp_nparams())
+
+
+def mlp_forward(params, X) -> np.ndarray:
+    P = np.ascontiguousarray(params, dtype=np.float64)
+    Xv = np.ascontiguousarray(X, dtype=np.float64).reshape(-1, 3)
+    out = np.empty(Xv.shape[0])
+    _check(load().orc_mlp_forward(_ptr(P), Xv.shape[0], _ptr(Xv), _ptr(out)), "orc_mlp_forward")
+    return out
+
+
+def mlp_grad(params, X, y):
+    """(gradient of mean 1/2 (s - y)^2 w.r.t. the parameters, loss)."""
+    P = np.ascontiguousarray(params, dtype=np.float64)
+    Xv = np.ascontiguousarray(X, dtype=np.float64).reshape(-1, 3)
+    yv = np.ascontiguousarray(y, dtype=np.float64)
+    G = np.empty_like(P)
+    loss = np.empty(1)
+    _check(load().orc_mlp_grad(_ptr(P), Xv.shape[0], _ptr(Xv), _ptr(yv), _ptr(G), _ptr(loss)), "orc_mlp_grad")
+    return G, float(loss[0])

@@ -372,3 +372,181 @@ int orc_objective(int N, const int64_t *I, const int *J, int R, double *const *A
   *out = err[2] + lambda_a * na + lambda_b * nb;
   return ORC_OK;
 }
+
+/* ======================================================================
+ * Learned per-row step sizes (not in the paper; an optional extension of the
+ * factor step of Eq. "Update_FastTuckerPlus_factor" with a per-row
+ * multiplier s: a <- a - gamma * s * g).
+ *
+ * Row statistics of mode n, row r, from the current A and B:
+ *   count_r  number of nonzeros whose mode-n index is r
+ *   g_r      sum over those nonzeros of the factor gradient
+ *            -e_m p_m + lambda a_r,  p_m = d_m B^(n)T   (Eq. "Gradient_low_rank_cp")
+ *   ebar_r   mean residual  sum e_m / count_r
+ *   gnorm_r  |g_r| / max(count_r, 1);  ema_r = beta ema_in_r + (1 - beta) gnorm_r
+ * Features: f0 = log(1 + count_r), f1 = log(1 + ema_r), f2 = ebar_r.
+ * Label: the exact line-search step of the row's convex subproblem
+ *   F_r(a) = sum_m [1/2 (x_m - a.p_m)^2 + 1/2 lambda |a|^2]
+ * along -g_r:  t* = |g|^2 / (sum_m (p_m.g)^2 + lambda count |g|^2), expressed
+ * as a multiplier of the epoch's SGD step gamma * g:  s* = t* / gamma, clipped
+ * to [1/4, 4]; rows without nonzeros (or with g = 0) get s* = 1.
+ * Rows of all modes are concatenated (mode 0 first).
+ * ====================================================================== */
+int orc_row_stats(int N, const int64_t *I, const int *J, int R, double *const *A,
+                  double *const *B, int64_t nnz, const int32_t *const *idx, const double *x,
+                  double lambda, double gamma, double beta, const double *ema_in,
+                  double *feat /* rows x 3 */, double *label /* rows, nullable */) {
+  if (orc_check_shape(N, J, R)) return ORC_EARG;
+  int64_t rows = 0, off[ORC_MAX_ORDER + 1];
+  int64_t goff[ORC_MAX_ORDER + 1];
+  off[0] = 0;
+  goff[0] = 0;
+  for (int n = 0; n < N; ++n) {
+    off[n + 1] = off[n] + I[n];
+    goff[n + 1] = goff[n] + I[n] * J[n];
+  }
+  rows = off[N];
+  double *cnt = (double *)calloc((size_t)rows, sizeof(double));
+  double *esum = (double *)calloc((size_t)rows, sizeof(double));
+  double *hsum = (double *)calloc((size_t)rows, sizeof(double));
+  double *g = (double *)calloc((size_t)goff[N], sizeof(double));
+  double *p = (double *)malloc(sizeof(double) * ORC_MAX_RANK);
+  int rc = ORC_OK;
+  if (!cnt || !esum || !hsum || !g || !p) { rc = ORC_ENOMEM; goto done; }
+  /* pass 1: counts, residual sums, row gradients */
+  for (int64_t m = 0; m < nnz; ++m) {
+    double c[ORC_MAX_ORDER * ORC_MAX_RANK], d[ORC_MAX_ORDER * ORC_MAX_RANK];
+    orc_c_rows(N, J, R, A, B, idx, m, c);
+    orc_d_rows(N, R, c, d);
+    double e = x[m] - orc_xhat(N, R, c);
+    for (int n = 0; n < N; ++n) {
+      int64_t row = idx[n][m];
+      const double *a = A[n] + row * J[n];
+      cnt[off[n] + row] += 1.0;
+      esum[off[n] + row] += e;
+      for (int j = 0; j < J[n]; ++j) {
+        double pj = 0.0;
+        for (int r = 0; r < R; ++r) pj += d[n * R + r] * B[n][(int64_t)j * R + r];
+        g[goff[n] + row * J[n] + j] += -e * pj + lambda * a[j];
+      }
+    }
+  }
+  /* pass 2: curvature along g, sum_m (p_m . g_r)^2 */
+  if (label) {
+    for (int64_t m = 0; m < nnz; ++m) {
+      double c[ORC_MAX_ORDER * ORC_MAX_RANK], d[ORC_MAX_ORDER * ORC_MAX_RANK];
+      orc_c_rows(N, J, R, A, B, idx, m, c);
+      orc_d_rows(N, R, c, d);
+      for (int n = 0; n < N; ++n) {
+        int64_t row = idx[n][m];
+        double q = 0.0;
+        for (int j = 0; j < J[n]; ++j) {
+          double pj = 0.0;
+          for (int r = 0; r < R; ++r) pj += d[n * R + r] * B[n][(int64_t)j * R + r];
+          q += pj * g[goff[n] + row * J[n] + j];
+        }
+        hsum[off[n] + row] += q * q;
+      }
+    }
+  }
+  for (int n = 0; n < N; ++n)
+    for (int64_t row = 0; row < I[n]; ++row) {
+      int64_t q = off[n] + row;
+      double gg = 0.0;
+      for (int j = 0; j < J[n]; ++j) {
+        double v = g[goff[n] + row * J[n] + j];
+        gg += v * v;
+      }
+      double k = cnt[q];
+      double gnorm = sqrt(gg) / (k > 1.0 ? k : 1.0);
+      double ema = ema_in ? beta * ema_in[q] + (1.0 - beta) * gnorm : gnorm;
+      feat[3 * q + 0] = log(1.0 + k);
+      feat[3 * q + 1] = log(1.0 + ema);
+      feat[3 * q + 2] = k > 0.0 ? esum[q] / k : 0.0;
+      if (label) {
+        double s = 1.0;
+        double den = hsum[q] + lambda * k * gg;
+        if (k > 0.0 && gg > 0.0 && den > 0.0) {
+          s = gg / den / gamma;
+          if (s < 0.25) s = 0.25;
+          if (s > 4.0) s = 4.0;
+        }
+        label[q] = s;
+      }
+    }
+done:
+  free(cnt); free(esum); free(hsum); free(g); free(p);
+  return rc;
+}
+
+/*
+ * Step-size network: features (3) -> 64 -> 64 -> 1 with ReLU, output
+ * s = 1/4 + 15/4 sigmoid(z) in (1/4, 4).  Parameters, in this order:
+ * W1 [64][3], b1 [64], W2 [64][64], b2 [64], w3 [64], b3 [1]  (4481 values).
+ */
+#define ORC_H 64
+#define ORC_NPARAM (ORC_H * 3 + ORC_H + ORC_H * ORC_H + ORC_H + ORC_H + 1)
+
+int orc_mlp_nparams(void) { return ORC_NPARAM; }
+
+static double orc_mlp_row(const double *P, const double *x, double *h1, double *h2, double *zout) {
+  const double *W1 = P, *b1 = W1 + ORC_H * 3, *W2 = b1 + ORC_H, *b2 = W2 + ORC_H * ORC_H;
+  const double *w3 = b2 + ORC_H, *b3 = w3 + ORC_H;
+  for (int i = 0; i < ORC_H; ++i) {
+    double s = b1[i];
+    for (int k = 0; k < 3; ++k) s += W1[i * 3 + k] * x[k];
+    h1[i] = s > 0.0 ? s : 0.0;
+  }
+  double z = b3[0];
+  for (int i = 0; i < ORC_H; ++i) {
+    double s = b2[i];
+    for (int j = 0; j < ORC_H; ++j) s += W2[i * ORC_H + j] * h1[j];
+    h2[i] = s > 0.0 ? s : 0.0;
+    z += w3[i] * h2[i];
+  }
+  *zout = z;
+  return 0.25 + 3.75 / (1.0 + exp(-z));
+}
+
+int orc_mlp_forward(const double *P, int64_t n, const double *X, double *s) {
+  double h1[ORC_H], h2[ORC_H], z;
+  for (int64_t m = 0; m < n; ++m) s[m] = orc_mlp_row(P, X + 3 * m, h1, h2, &z);
+  return ORC_OK;
+}
+
+/* Gradient of L = (1/n) sum_m 1/2 (s_m - y_m)^2 with respect to every
+ * parameter (same layout); *loss receives L. */
+int orc_mlp_grad(const double *P, int64_t n, const double *X, const double *y, double *G,
+                 double *loss) {
+  const double *W2 = P + ORC_H * 3 + ORC_H, *w3 = W2 + ORC_H * ORC_H + ORC_H;
+  double *gW1 = G, *gb1 = gW1 + ORC_H * 3, *gW2 = gb1 + ORC_H, *gb2 = gW2 + ORC_H * ORC_H;
+  double *gw3 = gb2 + ORC_H, *gb3 = gw3 + ORC_H;
+  double h1[ORC_H], h2[ORC_H], dh1[ORC_H], z, L = 0.0;
+  for (int q = 0; q < ORC_NPARAM; ++q) G[q] = 0.0;
+  for (int64_t m = 0; m < n; ++m) {
+    const double *x = X + 3 * m;
+    double s = orc_mlp_row(P, x, h1, h2, &z);
+    double sg = 1.0 / (1.0 + exp(-z));
+    double r = s - y[m];
+    L += 0.5 * r * r;
+    double dz = r * 3.75 * sg * (1.0 - sg) / (double)n;
+    gb3[0] += dz;
+    for (int j = 0; j < ORC_H; ++j) dh1[j] = 0.0;
+    for (int i = 0; i < ORC_H; ++i) {
+      gw3[i] += dz * h2[i];
+      double dh2 = h2[i] > 0.0 ? dz * w3[i] : 0.0;
+      gb2[i] += dh2;
+      for (int j = 0; j < ORC_H; ++j) {
+        gW2[i * ORC_H + j] += dh2 * h1[j];
+        dh1[j] += dh2 * W2[i * ORC_H + j];
+      }
+    }
+    for (int j = 0; j < ORC_H; ++j) {
+      double d = h1[j] > 0.0 ? dh1[j] : 0.0;
+      gb1[j] += d;
+      for (int k = 0; k < 3; ++k) gW1[j * 3 + k] += d * x[k];
+    }
+  }
+  *loss = n > 0 ? L / (double)n : 0.0;
+  return ORC_OK;
+}

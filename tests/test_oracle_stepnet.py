@@ -1,0 +1,144 @@
+"""Pins of the oracle's learned-step parts (row statistics, line-search
+labels, step-size network) against independent computations:
+
+* counts by np.bincount, residuals and row gradients by central finite
+  differences of the row's subproblem loss through the dense Tucker model;
+* the label is the exact minimiser along -g of that (quadratic) subproblem,
+  recovered from three loss evaluations;
+* the network's forward pass equals the textbook MLP written with numpy
+  matrix products, and its gradient equals central finite differences of the
+  oracle's own forward loss.
+"""
+import numpy as np
+
+import oracle
+from test_oracle_pins import dense_predict, rand_problem
+
+
+def row_loss(A, B, idx, x, lam, n, row, a_row):
+    """F_r(a) = sum over the row's nonzeros of 1/2 (x - xhat)^2 + 1/2 lam |a|^2."""
+    A2 = [a.copy() for a in A]
+    A2[n][row] = a_row
+    tot = 0.0
+    for m in np.nonzero(idx[n] == row)[0]:
+        e = x[m] - dense_predict(A2, B, idx[:, m])
+        tot += 0.5 * e * e + 0.5 * lam * float(a_row @ a_row)
+    return tot
+
+
+def test_row_stats_against_definitions():
+    rng = np.random.default_rng(3)
+    N, J, R = 3, (2, 3, 2), 3
+    I = [4, 5, 3]
+    A, B, idx, x = rand_problem(rng, N, I, J, R, 30, scale=0.6)
+    lam, gamma, beta = 0.1, 0.05, 0.3
+    ema_in = rng.uniform(0, 1, sum(I))
+    feat, lab = oracle.row_stats(A, B, idx, x, lam, gamma, beta, ema_in)
+    xhat = np.array([dense_predict(A, B, idx[:, m]) for m in range(len(x))])
+    e = x - xhat
+    off = 0
+    h = 1e-6
+    for n in range(N):
+        cnt = np.bincount(idx[n], minlength=I[n])
+        for r in range(I[n]):
+            q = off + r
+            assert np.isclose(feat[q, 0], np.log1p(cnt[r]), rtol=1e-14)
+            mean_e = e[idx[n] == r].mean() if cnt[r] else 0.0
+            assert np.isclose(feat[q, 2], mean_e, rtol=1e-10, atol=1e-12)
+            # row gradient by central differences
+            g = np.zeros(J[n])
+            for j in range(J[n]):
+                ap, am = A[n][r].copy(), A[n][r].copy()
+                ap[j] += h
+                am[j] -= h
+                g[j] = (row_loss(A, B, idx, x, lam, n, r, ap) - row_loss(A, B, idx, x, lam, n, r, am)) / (2 * h)
+            gnorm = np.linalg.norm(g) / max(cnt[r], 1)
+            ema = beta * ema_in[q] + (1 - beta) * gnorm
+            assert np.isclose(feat[q, 1], np.log1p(ema), rtol=1e-6, atol=1e-9)
+            # exact line search along -g from three loss values (F is quadratic in t)
+            if cnt[r] == 0 or np.linalg.norm(g) < 1e-12:
+                assert lab[q] == 1.0
+                continue
+            dlt = 1e-3
+            f0 = row_loss(A, B, idx, x, lam, n, r, A[n][r])
+            fp = row_loss(A, B, idx, x, lam, n, r, A[n][r] - dlt * g)
+            fm = row_loss(A, B, idx, x, lam, n, r, A[n][r] + dlt * g)
+            t_star = dlt * (fm - fp) / (2 * (fp - 2 * f0 + fm))
+            want = float(np.clip(t_star / gamma, 0.25, 4.0))
+            assert np.isclose(lab[q], want, rtol=1e-5), (n, r, lab[q], want)
+        off += I[n]
+
+
+def mlp_numpy(P, X):
+    H = 64
+    W1 = P[:H * 3].reshape(H, 3)
+    b1 = P[H * 3:H * 4]
+    W2 = P[H * 4:H * 4 + H * H].reshape(H, H)
+    b2 = P[H * 4 + H * H:H * 5 + H * H]
+    w3 = P[H * 5 + H * H:H * 6 + H * H]
+    b3 = P[H * 6 + H * H]
+    h1 = np.maximum(0.0, X @ W1.T + b1)
+    h2 = np.maximum(0.0, h1 @ W2.T + b2)
+    z = h2 @ w3 + b3
+    return 0.25 + 3.75 / (1.0 + np.exp(-z))
+
+
+def test_mlp_forward_is_the_textbook_network():
+    rng = np.random.default_rng(4)
+    P = rng.normal(0, 0.3, oracle.mlp_nparams())
+    X = rng.normal(0, 1, (50, 3))
+    np.testing.assert_allclose(oracle.mlp_forward(P, X), mlp_numpy(P, X), rtol=1e-12)
+
+
+def test_mlp_gradient_by_central_differences():
+    rng = np.random.default_rng(5)
+    n_par = oracle.mlp_nparams()
+    P = rng.normal(0, 0.3, n_par)
+    X = rng.normal(0, 1, (20, 3))
+    y = rng.uniform(0.25, 4, 20)
+    G, loss = oracle.mlp_grad(P, X, y)
+    assert np.isclose(loss, np.mean(0.5 * (oracle.mlp_forward(P, X) - y) ** 2), rtol=1e-12)
+    h = 1e-6
+    pick = np.concatenate([np.arange(0, 192, 17), np.arange(192, 256, 7), np.arange(256, 4352, 97),
+                           np.arange(4352, 4481, 11), [4480]])
+    for q in pick:
+        Pp, Pm = P.copy(), P.copy()
+        Pp[q] += h
+        Pm[q] -= h
+        fd = (oracle.mlp_grad(Pp, X, y)[1] - oracle.mlp_grad(Pm, X, y)[1]) / (2 * h)
+        assert np.isclose(G[q], fd, rtol=1e-5, atol=1e-9), q
+
+
+STEPNET_PINS = [test_row_stats_against_definitions, test_mlp_forward_is_the_textbook_network,
+                test_mlp_gradient_by_central_differences]
+STEPNET_MUTANTS = [
+    ("label_without_regulariser_curvature", "double den = hsum[q] + lambda * k * gg;", "double den = hsum[q];"),
+    ("relu_derivative_dropped", "double dh2 = h2[i] > 0.0 ? dz * w3[i] : 0.0;", "double dh2 = dz * w3[i];"),
+    ("output_range_wrong", "return 0.25 + 3.75 / (1.0 + exp(-z));", "return 0.25 + 4.0 / (1.0 + exp(-z));"),
+    ("row_gradient_sign", "g[goff[n] + row * J[n] + j] += -e * pj + lambda * a[j];",
+     "g[goff[n] + row * J[n] + j] += e * pj + lambda * a[j];"),
+    ("mean_residual_not_divided", "feat[3 * q + 2] = k > 0.0 ? esum[q] / k : 0.0;", "feat[3 * q + 2] = esum[q];"),
+]
+
+
+def test_planted_mistakes_break_a_stepnet_pin(tmp_path):
+    import subprocess
+    src = open(oracle._SRC).read()
+    survivors = []
+    for name, old, new in STEPNET_MUTANTS:
+        assert src.count(old) == 1, f"mutation anchor for {name} not found"
+        msrc = tmp_path / f"{name}.c"
+        msrc.write_text(src.replace(old, new, 1))
+        so = tmp_path / f"{name}.so"
+        subprocess.run(["gcc", *oracle.CFLAGS, str(msrc), "-o", str(so), "-lm"], check=True)
+        caught = False
+        with oracle.use_library(str(so)):
+            for pin in STEPNET_PINS:
+                try:
+                    pin()
+                except AssertionError:
+                    caught = True
+                    break
+        if not caught:
+            survivors.append(name)
+    assert not survivors, survivors
