@@ -31,9 +31,11 @@ def test_row_stats_against_definitions():
     N, J, R = 3, (2, 3, 2), 3
     I = [4, 5, 3]
     A, B, idx, x = rand_problem(rng, N, I, J, R, 30, scale=0.6)
-    lam, gamma, beta = 0.1, 0.05, 0.3
+    lam, gamma, beta = 0.1, 1.0, 0.3
     ema_in = rng.uniform(0, 1, sum(I))
     feat, lab = oracle.row_stats(A, B, idx, x, lam, gamma, beta, ema_in)
+    # most labels inside the clip range, so the formula itself is exercised
+    assert np.mean((lab > 0.25) & (lab < 4.0)) > 0.8
     xhat = np.array([dense_predict(A, B, idx[:, m]) for m in range(len(x))])
     e = x - xhat
     off = 0
