@@ -245,6 +245,50 @@ ft_status ft_predict(ft_ctx *ctx, int64_t n, const int32_t *const *idx, float *o
 ft_status ft_rmse(ft_ctx *ctx, int64_t n, const int32_t *const *idx, const float *vals,
                   double *out3, void *stream);
 
+/* Inputs of the learned per-row step size (an extension: the paper uses
+ * one step size, Eq. "Update_FastTuckerPlus_factor").  For every row of every
+ * mode (rows concatenated, mode 0 first, sum I_n rows), from the current A, B:
+ *   count, mean residual, and the row gradient g = sum_m (-e_m p_m + lambda_a a)
+ *   (Eq. "Gradient_low_rank_cp" summed over the row's training nonzeros);
+ *   features[3 r .. 3 r + 2] = {log(1 + count), log(1 + ema), mean residual}
+ *   with ema <- ema_beta * ema + (1 - ema_beta) |g| / max(count, 1) (ema: device,
+ *   rows, in/out; NULL = no history, ema = |g| / count);
+ *   labels[r] (NULL = not computed): the exact line-search step along -g of
+ *   the row's subproblem sum_m [1/2 (x_m - a.p_m)^2 + 1/2 lambda_a |a|^2],
+ *   |g|^2 / (sum_m (p_m.g)^2 + lambda_a count |g|^2), divided by lr_a and
+ *   clipped to [1/4, 4] (1 for rows without nonzeros).
+ * FP32 with atomic accumulation (the summation order varies between runs). */
+ft_status ft_row_stats(ft_ctx *ctx, float lambda_a, float lr_a, float ema_beta, float *ema,
+                       float *features, float *labels, void *stream);
+
+/* ------------------------------------------------------- step-size network
+ * A small MLP (3 -> 64 -> 64 -> 1, ReLU, output s = 1/4 + 15/4 sigmoid(z))
+ * that maps the row features of ft_row_stats to per-row step multipliers for
+ * ft_epoch_factors (row_step_scale).  Not in the paper.  All state lives in
+ * one caller-allocated device buffer of ft_stepnet_bytes() bytes (16-byte
+ * aligned): FP32 master parameters, their BF16 copies (used by every kernel,
+ * with FP32 accumulation), Adam moments and the last gradient.  Parameter
+ * order: W1 [64][3], b1 [64], W2 [64][64], b2 [64], w3 [64], b3. */
+size_t ft_stepnet_bytes(void);
+
+/* Initialise the buffer: He-uniform weights from a counter-based hash of
+ * (seed, index), zero biases except b3 = log(1/4), so s starts near 1. */
+ft_status ft_stepnet_init(void *net, uint64_t seed, void *stream);
+
+/* scale[r] = s(features[3 r .. 3 r + 2]) for r < rows (device arrays). */
+ft_status ft_stepnet_forward(const void *net, int64_t rows, const float *features, float *scale,
+                             void *stream);
+
+/* `steps` full-batch Adam steps (lr, betas 0.9 / 0.999, eps 1e-8) on the mean
+ * of 1/2 (s - label)^2 over `rows` samples.  loss_out (host, nullable)
+ * receives the loss of the last step's forward pass (synchronises). */
+ft_status ft_stepnet_train(void *net, int64_t rows, const float *features, const float *labels,
+                           float lr, int steps, double *loss_out, void *stream);
+
+/* Copy 4481 values to host memory: which = 0 FP32 masters, 1 the BF16
+ * copies (widened), 2 the gradient of the last training step.  Synchronises. */
+ft_status ft_stepnet_get(const void *net, int which, float *out_host, void *stream);
+
 /* Synchronise the stream and report (then clear) the latched device error. */
 ft_status ft_check(ft_ctx *ctx, void *stream);
 

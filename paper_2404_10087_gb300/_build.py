@@ -25,7 +25,7 @@ NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompil
               f"-I{INCLUDE}", f"-I{CSRC}"]
 
 # (source, extra defines, object name)
-UNITS = [("ft_api.cu", [], "ft_api"), ("ft_batch.cu", [], "ft_batch")]
+UNITS = [("ft_api.cu", [], "ft_api"), ("ft_batch.cu", [], "ft_batch"), ("ft_stepnet.cu", [], "ft_stepnet")]
 # the slowest units first, so a parallel build finishes early
 for _m in (0, 1, 2):
     for _k in (32, 16):

@@ -170,6 +170,46 @@ __global__ void k_remap(const RemapArgs a) {
     }
 }
 
+struct RowFinishArgs {
+  const float *gsum, *cnt, *esum, *hsum;
+  int N;
+  int J[FT_MAXN];
+  int64_t roff[FT_MAXN + 1];
+  int64_t goff[FT_MAXN];
+  float lambda, gamma, beta;
+  float *ema;      // nullable, in/out
+  float *feat;     // rows x 3
+  float *label;    // nullable
+};
+
+// Features and labels of every row from the accumulated statistics:
+// f0 = log(1 + count), f1 = log(1 + ema of |g| / count), f2 = mean residual;
+// label = exact line-search step along -g of the row's subproblem divided by
+// the step size, clipped to [1/4, 4] (1 for rows without nonzeros).
+__global__ void k_row_finish(const RowFinishArgs a) {
+  const int64_t q = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (q >= a.roff[a.N]) return;
+  int n = 0;
+  while (q >= a.roff[n + 1]) ++n;
+  const int64_t row = q - a.roff[n];
+  const float *g = a.gsum + a.goff[n] + row * a.J[n];
+  float gg = 0.f;
+  for (int j = 0; j < a.J[n]; ++j) gg = fmaf(g[j], g[j], gg);
+  const float k = a.cnt[q];
+  const float gnorm = sqrtf(gg) / fmaxf(k, 1.f);
+  const float ema = a.ema ? a.beta * a.ema[q] + (1.f - a.beta) * gnorm : gnorm;
+  if (a.ema) a.ema[q] = ema;
+  a.feat[3 * q + 0] = log1pf(k);
+  a.feat[3 * q + 1] = log1pf(ema);
+  a.feat[3 * q + 2] = k > 0.f ? a.esum[q] / k : 0.f;
+  if (a.label) {
+    float sc = 1.f;
+    const float den = a.hsum[q] + a.lambda * k * gg;
+    if (k > 0.f && gg > 0.f && den > 0.f) sc = fminf(fmaxf(gg / den / a.gamma, 0.25f), 4.f);
+    a.label[q] = sc;
+  }
+}
+
 // ------------------------------------------------------------------- plan
 struct Plan {
   int N = 0, R = 0, K = 0, sumJ = 0;
@@ -188,7 +228,8 @@ struct Plan {
   // workspace offsets
   size_t off_err = 0, off_out = 0, off_partial = 0, off_errpart = 0, off_delta = 0;
   size_t off_order = 0, off_segptr = 0, off_segrow = 0;
-  size_t off_remap = 0, off_hot = 0, off_counts = 0, total = 0;
+  size_t off_remap = 0, off_hot = 0, off_counts = 0, off_stats = 0, total = 0;
+  int64_t rows = 0, grows = 0;      // sum I_n and sum I_n J_n
 };
 
 // Shared memory of the hot-row cache: with two 256-thread CTAs per SM (the
@@ -295,6 +336,13 @@ ft_status make_plan(int N, const int64_t *I, const int *J, int R, int64_t nnz, c
     p->off_segptr = off; off += align_up(sizeof(int32_t) * size_t(N) * (nnz + 1));
     p->off_segrow = off; off += align_up(sizeof(int32_t) * size_t(N) * std::max<int64_t>(nnz, 1));
   }
+  p->rows = 0;
+  p->grows = 0;
+  for (int n = 0; n < N; ++n) {
+    p->rows += I[n];
+    p->grows += I[n] * J[n];
+  }
+  p->off_stats = off; off += align_up(sizeof(float) * size_t(p->grows + 3 * p->rows));
   p->total = off;
   return FT_OK;
 }
@@ -833,6 +881,58 @@ ft_status ft_rmse(ft_ctx *c, int64_t n, const int32_t *const *idx, const float *
   if (cudaMemcpyAsync(out3, fa.out3, sizeof(double) * 3, cudaMemcpyDeviceToHost, st) != cudaSuccess)
     return FT_ERR_CUDA;
   return take_error(c, st);
+}
+
+ft_status ft_row_stats(ft_ctx *c, float lambda_a, float lr_a, float ema_beta, float *ema, float *features,
+                       float *labels, void *stream) {
+  if (!c || !features || !(lr_a > 0.f) || !std::isfinite(lambda_a) || !(ema_beta >= 0.f && ema_beta <= 1.f))
+    return FT_ERR_ARG;
+  const Plan &p = c->p;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  float *base = ws_ptr<float>(c, p.off_stats);
+  if (cudaMemsetAsync(base, 0, sizeof(float) * size_t(p.grows + 3 * p.rows), st) != cudaSuccess) return FT_ERR_CUDA;
+  ft::RowStatArgs s;
+  memset(&s, 0, sizeof(s));
+  s.p = base_args(c);
+  s.p.lam = lambda_a;
+  s.gsum = base;
+  s.cnt = base + p.grows;
+  s.esum = s.cnt + p.rows;
+  s.hsum = s.esum + p.rows;
+  int64_t ro = 0, go = 0;
+  for (int n = 0; n < p.N; ++n) {
+    s.roff[n] = ro;
+    s.goff[n] = go;
+    ro += p.I[n];
+    go += p.I[n] * p.J[n];
+  }
+  const int grid = p.num_sms * 4;
+  ft_status st1 = FT_OK;
+  if (p.nnz > 0) {
+    st1 = launch(c, p.es.row_stats1, grid, 256, p.es.stats_smem, &s, st);
+    if (st1 == FT_OK && labels) st1 = launch(c, p.es.row_stats2, grid, 256, p.es.stats_smem, &s, st);
+    if (st1 != FT_OK) return st1;
+  }
+  RowFinishArgs f;
+  memset(&f, 0, sizeof(f));
+  f.gsum = s.gsum;
+  f.cnt = s.cnt;
+  f.esum = s.esum;
+  f.hsum = s.hsum;
+  f.N = p.N;
+  for (int n = 0; n < p.N; ++n) {
+    f.J[n] = p.J[n];
+    f.roff[n] = s.roff[n];
+    f.goff[n] = s.goff[n];
+  }
+  f.roff[p.N] = p.rows;
+  f.lambda = lambda_a;
+  f.gamma = lr_a;
+  f.beta = ema_beta;
+  f.ema = ema;
+  f.feat = features;
+  f.label = labels;
+  return launch(c, reinterpret_cast<const void *>(&k_row_finish), int((p.rows + 255) / 256), 256, 0, &f, st);
 }
 
 ft_status ft_check(ft_ctx *c, void *stream) {

@@ -1194,3 +1194,73 @@ __global__ void __launch_bounds__(256) k_batch_core(const BatchArgs b) {
 }
 
 }  // namespace ft
+
+// ======================================================== per-row statistics
+// Inputs of the learned step size: for every row of every mode, the number of
+// nonzeros, the residual sum and the full row gradient
+//   g_r = sum_m (-e_m p_m + lambda a_r),  p_m = d_m B^(n)T   (Eq. "Gradient_low_rank_cp")
+// (PASS 1), and the curvature along g_r, sum_m (p_m . g_r)^2 (PASS 2),
+// accumulated with float atomics.  FP32 on the CUDA cores.
+namespace ft {
+
+struct RowStatArgs {
+  EpochArgs p;
+  float *gsum;                 // row gradients, mode n at goff[n] (I_n x J_n)
+  float *cnt, *esum, *hsum;    // per row (rows of all modes concatenated)
+  int64_t roff[FT_MAXN];
+  int64_t goff[FT_MAXN];
+};
+
+template <int N, int K, int PASS>
+__global__ void __launch_bounds__(256) k_row_stats(const RowStatArgs s) {
+  extern __shared__ __align__(16) float smem[];
+  constexpr int CPL = K / 4;
+  constexpr int TW = Prod<K, MATH_FP32>::WORDS;
+  const EpochArgs &p = s.p;
+  fill_tables<N, K, MATH_FP32>(smem, p, true);
+  __syncthreads();
+  const int lane = threadIdx.x & 31, t = lane & 3;
+  const int64_t warp = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = (int64_t(gridDim.x) * blockDim.x) >> 5;
+  const int64_t ntiles = (p.end - p.begin + FT_TILE - 1) / FT_TILE;
+  for (int64_t tile = warp; tile < ntiles; tile += nwarps) {
+    Front<N, K, MATH_FP32, true> f;
+    f.load(p, p.begin + tile * FT_TILE, lane, true);
+    f.compute(smem, TW, lane);
+    const float e[2] = {f.x[0] - f.xhat[0], f.x[1] - f.xhat[1]};
+#pragma unroll
+    for (int n = 0; n < N; ++n) {
+      float d[2][CPL], pp[2][CPL];
+      f.leave_one_out(n, d);
+      Prod<K, MATH_FP32>::run(d, smem + (N + n) * TW, pp, lane);
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int64_t row = f.row[n][h];
+        float *g = s.gsum + s.goff[n] + row * p.J[n] + CPL * t;
+        if constexpr (PASS == 1) {
+          if (f.valid[h]) {
+#pragma unroll
+            for (int q = 0; q < CPL; ++q)
+              if (CPL * t + q < p.J[n]) atomicAdd(g + q, fmaf(-e[h], pp[h][q], p.lam * f.a[n][h][q]));
+            if (t == 0) {
+              atomicAdd(s.cnt + s.roff[n] + row, 1.f);
+              atomicAdd(s.esum + s.roff[n] + row, e[h]);
+            }
+          }
+        } else {
+          float q2 = 0.f;
+          if (f.valid[h]) {
+#pragma unroll
+            for (int q = 0; q < CPL; ++q)
+              if (CPL * t + q < p.J[n]) q2 = fmaf(pp[h][q], g[q], q2);
+          }
+          q2 += __shfl_xor_sync(FULL, q2, 1);
+          q2 += __shfl_xor_sync(FULL, q2, 2);
+          if (t == 0 && f.valid[h]) atomicAdd(s.hsum + s.roff[n] + row, q2 * q2);
+        }
+      }
+    }
+  }
+}
+
+}  // namespace ft

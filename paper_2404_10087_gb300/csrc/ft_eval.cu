@@ -17,6 +17,9 @@ ft::EvalSet make_eval() {
   s.predict = reinterpret_cast<const void *>(&ft::k_eval<N, FT_K, 0>);
   s.errors = reinterpret_cast<const void *>(&ft::k_eval<N, FT_K, 1>);
   s.smem = size_t(N) * ft::Prod<FT_K, ft::MATH_FP32>::WORDS * sizeof(float);
+  s.row_stats1 = reinterpret_cast<const void *>(&ft::k_row_stats<N, FT_K, 1>);
+  s.row_stats2 = reinterpret_cast<const void *>(&ft::k_row_stats<N, FT_K, 2>);
+  s.stats_smem = 2 * s.smem;
   return s;
 }
 }  // namespace

@@ -21,11 +21,14 @@ struct KernelSet {
   int batch_core_threads = 256;
 };
 
-// FP32 prediction / error kernels of one (N, K).
+// FP32 prediction / error / row-statistics kernels of one (N, K).
 struct EvalSet {
   const void *predict = nullptr;
   const void *errors = nullptr;
   size_t smem = 0;
+  const void *row_stats1 = nullptr;   // row gradients, counts, residual sums
+  const void *row_stats2 = nullptr;   // curvature along the row gradients
+  size_t stats_smem = 0;
 };
 
 }  // namespace ft

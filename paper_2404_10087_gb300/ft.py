@@ -33,7 +33,8 @@ EXPORTS = ["ft_config_default", "ft_workspace_size", "ft_init", "ft_epoch_factor
            "ft_launch_count", "ft_destroy", "ft_status_str", "ft_core_grad_noalloc",
            "ft_batch_workspace_size", "ft_batch_init", "ft_batch_tune", "ft_batch_epoch",
            "ft_batch_rmse", "ft_batch_num_classes", "ft_batch_class_info", "ft_batch_launch_count",
-           "ft_batch_destroy"]
+           "ft_batch_destroy", "ft_row_stats", "ft_stepnet_bytes", "ft_stepnet_init",
+           "ft_stepnet_forward", "ft_stepnet_train", "ft_stepnet_get"]
 
 
 class FtError(RuntimeError):
@@ -106,6 +107,12 @@ def _declare(lib):
         "ft_batch_class_info": (INT, [_P, INT, _P]),
         "ft_batch_launch_count": (I64, [_P]),
         "ft_batch_destroy": (None, [_P]),
+        "ft_row_stats": (INT, [_P, FLT, FLT, FLT, _P, _P, _P, _P]),
+        "ft_stepnet_bytes": (ctypes.c_size_t, []),
+        "ft_stepnet_init": (INT, [_P, ctypes.c_uint64, _P]),
+        "ft_stepnet_forward": (INT, [_P, I64, _P, _P, _P]),
+        "ft_stepnet_train": (INT, [_P, I64, _P, _P, FLT, INT, _P, _P]),
+        "ft_stepnet_get": (INT, [_P, INT, _P, _P]),
     }
     for name, (res, args) in sigs.items():
         f = getattr(lib, name)
@@ -418,3 +425,50 @@ class FastTuckerBatch:
             self.close()
         except Exception:
             pass
+
+
+# ------------------------------------------------------- learned step sizes
+STEPNET_PARAMS = 4481
+
+
+def ft_row_stats(ctx, lambda_a, lr_a, ema_beta, ema, features, labels=None, stream=None):
+    _check(load().ft_row_stats(ctx, float(lambda_a), float(lr_a), float(ema_beta),
+                               None if ema is None else ema.data_ptr(), features.data_ptr(),
+                               None if labels is None else labels.data_ptr(), _stream(stream)),
+           "ft_row_stats")
+
+
+def ft_stepnet_bytes() -> int:
+    return int(load().ft_stepnet_bytes())
+
+
+def ft_stepnet_init(net, seed=0, stream=None):
+    _check(load().ft_stepnet_init(net.data_ptr(), int(seed), _stream(stream)), "ft_stepnet_init")
+
+
+def ft_stepnet_forward(net, features, scale, stream=None):
+    rows = int(scale.numel())
+    _check(load().ft_stepnet_forward(net.data_ptr(), rows, features.data_ptr() if rows else None,
+                                     scale.data_ptr() if rows else None, _stream(stream)), "ft_stepnet_forward")
+
+
+def ft_stepnet_train(net, features, labels, lr, steps, stream=None):
+    loss = ctypes.c_double(0.0)
+    _check(load().ft_stepnet_train(net.data_ptr(), int(labels.numel()), features.data_ptr(), labels.data_ptr(),
+                                   float(lr), int(steps), ctypes.byref(loss), _stream(stream)),
+           "ft_stepnet_train")
+    return float(loss.value)
+
+
+def ft_stepnet_get(net, which, stream=None):
+    import numpy as np
+    out = np.empty(STEPNET_PARAMS, dtype=np.float32)
+    _check(load().ft_stepnet_get(net.data_ptr(), int(which), out.ctypes.data, _stream(stream)), "ft_stepnet_get")
+    return out
+
+
+def new_stepnet(device, seed=0):
+    """A device buffer holding an initialised step-size network."""
+    net = torch.empty(ft_stepnet_bytes(), dtype=torch.uint8, device=device)
+    ft_stepnet_init(net, seed)
+    return net
