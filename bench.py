@@ -36,8 +36,12 @@ from paper_2404_10087_gb300 import ft, synth  # noqa: E402
 METRIC = "SGD nonzero-updates/sec (factor+core) at J=R=16; time-to-RMSE vs plain FP32"
 UNIT = "nnz-updates/s"
 WORKLOAD = "netflix_shaped_zipf_1e8"
-LR = 0.01          # factor step gamma_A
-LR_B = 1.0         # core step gamma_B: Algorithm 5 divides the summed gradient by |Omega|
+# Step sizes of the Netflix-shaped workload (the paper's are unstated), picked
+# by a short sweep for a smooth test-RMSE curve; the core step is on the scale
+# of a full-gradient step because Algorithm 5 divides the summed gradient by
+# |Omega|.
+LR = 0.005         # factor step gamma_A
+LR_B = 0.3         # core step gamma_B
 LAM = 0.01
 FALLBACK_HBM_GBS = 6800.0
 
@@ -356,15 +360,74 @@ def run_ours(args, rank, world, local_rank):
     }
     if not args.no_time_to_rmse:
         out["time_to_rmse"] = time_to_rmse(w, tri, trx, tei, tex, dev, args.ttr_epochs, args.precision)
+        out["learned_step"] = learned_step_ab(dev)
     if not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(args.cpu_sample)
     return out
 
 
-def time_to_rmse(w, tri, trx, tei, tex, dev, epochs, precision):
+def learned_step_ab(dev, epochs=20, lr=0.01, lam=0.01):
+    """Planted 3-order tensor (1e5 uniform coordinates, planted J = R = 4, noise
+    0.1), eta = lambda = 0.01 for factors and cores: epochs and wall time for
+    the learned per-row step size to reach the plain FP32 method's test RMSE
+    after `epochs` epochs.  The network is trained on traces of a plain run
+    from another start; its statistics and network passes are timed."""
+    from paper_2404_10087_gb300 import learned_step as ls
+    w = synth.WORKLOADS["planted_uniform_1e5"]
+    d = synth.draw_workload(w, device=dev)
+    allidx = [d.idx[n].contiguous() for n in range(w.N)]
+    pm = ft.FastTuckerPlus(allidx, torch.zeros(d.idx.shape[1], device=dev),
+                           [a.contiguous() for a in d.planted_A], [b.contiguous() for b in d.planted_B], hot_rows=0)
+    x = pm.predict(allidx) + d.noise
+    pm.close()
+    tri = [d.idx[n, d.train].contiguous() for n in range(w.N)]
+    tei = [d.idx[n, d.test].contiguous() for n in range(w.N)]
+    xtr, xte = x[d.train].contiguous(), x[d.test].contiguous()
+
+    def start(off):
+        return synth.initial_factors(w, device=dev, seed_offset=off)
+
+    def timed(step, model, target=None):
+        torch.cuda.synchronize()
+        t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        t0.record()
+        r, ep = None, 0
+        for ep in range(1, epochs + 1):
+            step()
+            r = model.rmse(tei, xte)[0]
+            if target is not None and r <= target:
+                break
+        t1.record()
+        t1.synchronize()
+        return ep, t0.elapsed_time(t1) / 1e3, r
+
+    A, B = start(1)
+    plain = ft.FastTuckerPlus(tri, xtr, A, B)
+    ep_p, t_p, target = timed(lambda: (plain.epoch_factors(lr, lam), plain.epoch_core(lr, lam)), plain)
+    A, B = start(7)
+    feats, labels = ls.collect_traces(ft.FastTuckerPlus(tri, xtr, A, B), 10, lr, lam, lr, lam)
+    net = ft.new_stepnet(dev, seed=0)
+    curve = ls.train(net, feats, labels, steps=400, lr=3e-3)
+    A, B = start(1)
+    model = ft.FastTuckerPlus(tri, xtr, A, B)
+    learned = ls.LearnedStep(model, net, lr, lam)
+    ep_l, t_l, r_l = timed(lambda: learned.epoch(lr, lam), model, target)
+    reached = r_l <= target
+    return {"workload": "planted_uniform_1e5", "target_test_rmse": target, "plain_epochs": ep_p,
+            "plain_seconds": t_p, "learned_epochs": ep_l if reached else None,
+            "learned_seconds": t_l if reached else None, "reached": reached,
+            "speedup": (t_p / t_l) if reached else None, "trace_rows": int(labels.numel()),
+            "net_train_loss": [round(v, 5) for v in curve]}
+
+
+def time_to_rmse(w, tri, trx, tei, tex, dev, epochs, precision, window=3):
     """Wall time for the mixed-precision run to reach the test RMSE that plain
     FP32 (CUDA cores) reaches after `epochs` epochs, both from the same start.
-    An epoch is factor phase + core phase + test RMSE; times are CUDA events."""
+    Hogwild test RMSE wobbles from epoch to epoch, so both sides use the mean
+    over the last `window` epochs: the target is the FP32 run's final window
+    mean, and the candidate is done at the first epoch whose window mean is at
+    or below it.  An epoch is factor phase + core phase + test RMSE; times are
+    CUDA events."""
     A0, B0 = synth.initial_factors(w, device=dev, mean_value=float(trx.double().mean()))
 
     def run(prec, max_epochs, target=None):
@@ -385,17 +448,17 @@ def time_to_rmse(w, tri, trx, tei, tex, dev, epochs, precision):
             t1.synchronize()
             curve.append(r)
             times.append(t0.elapsed_time(t1) / 1e3)
-            if target is not None and r <= target:
+            if target is not None and len(curve) >= window and sum(curve[-window:]) / window <= target:
                 break
         m.close()
         return curve, times
 
     base_curve, base_times = run("fp32", epochs)
-    target = base_curve[-1]
+    target = sum(base_curve[-window:]) / window
     fast_curve, fast_times = run(precision, 3 * epochs, target)
-    reached = fast_curve[-1] <= target
+    reached = len(fast_curve) >= window and sum(fast_curve[-window:]) / window <= target
     return {
-        "target_test_rmse": target, "baseline": "fp32", "candidate": precision,
+        "target_test_rmse": target, "window": window, "baseline": "fp32", "candidate": precision,
         "baseline_epochs": len(base_curve), "baseline_seconds": base_times[-1],
         "candidate_epochs": len(fast_curve), "candidate_seconds": fast_times[-1] if reached else None,
         "reached": reached,
