@@ -397,7 +397,19 @@ struct Front {
     for (int n = 0; n < N; ++n)
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
-        if ((hot >> (2 * n + h)) & 1u) {
+        const bool is_hot = (hot >> (2 * n + h)) & 1u;
+        if (rep != nullptr && ((p.vecmask >> n) & 1) != 0) {
+          // full-width rows: one generic 16-byte load from the cache or from
+          // global memory (a select, not a divergent branch)
+          const float *src = is_hot ? rep + size_t(row[n][h]) * K + CPL * t
+                                    : p.A[n] + int64_t(row[n][h]) * p.J[n] + CPL * t;
+#pragma unroll
+          for (int w = 0; w < CPL; w += 4) {
+            float4 f4 = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (valid[h]) f4 = *reinterpret_cast<const float4 *>(src + w);
+            a[n][h][w] = f4.x; a[n][h][w + 1] = f4.y; a[n][h][w + 2] = f4.z; a[n][h][w + 3] = f4.w;
+          }
+        } else if (is_hot) {
           const float *src = rep + size_t(row[n][h]) * K + CPL * t;
 #pragma unroll
           for (int w = 0; w < CPL; w += 4) {
@@ -554,7 +566,15 @@ __device__ __forceinline__ void factor_tile(const EpochArgs &p, const float *tab
 #pragma unroll
         for (int q = 0; q < CPL; ++q)
           out[q] = fmaf(lr, fmaf(e[h], pp[h][q], -p.lam * f.a[n][h][q]), f.a[n][h][q]);
-        if (is_hot) {
+        if (rep != nullptr && ((p.vecmask >> n) & 1) != 0) {
+          // one generic 16-byte store to the cache or to global memory
+          float *dst = is_hot ? rep + size_t(f.row[n][h]) * K + CPL * t
+                              : p.A[n] + int64_t(f.row[n][h]) * p.J[n] + CPL * t;
+#pragma unroll
+          for (int w = 0; w < CPL; w += 4)
+            *reinterpret_cast<float4 *>(dst + w) = make_float4(out[w], out[w + 1], out[w + 2], out[w + 3]);
+          if (is_hot && t == 0) dirty[f.row[n][h]] = 1;
+        } else if (is_hot) {
           float *dst = rep + size_t(f.row[n][h]) * K + CPL * t;
 #pragma unroll
           for (int w = 0; w < CPL; w += 4)
