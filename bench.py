@@ -156,8 +156,9 @@ def aggregate_replicas(times_ms, units_per_rank, steps, world, device="cpu"):
 def make_workload(device, nnz=None, name=WORKLOAD):
     """Draw the synthetic tensor on `device`; planted values are computed by the
     library's own predict call, then mapped to integer ratings 1..5 (ratings
-    workloads) or given the workload's noise."""
-    w = synth.WORKLOADS[name]
+    workloads) or given the workload's noise.  `name` is a recipe name or a
+    synth.Workload."""
+    w = synth.WORKLOADS[name] if isinstance(name, str) else name
     d = synth.draw_workload(w, device=device, nnz=nnz)
     N = w.N
     allidx = [d.idx[n].contiguous() for n in range(N)]
@@ -250,7 +251,7 @@ def run_ours(args, rank, world, local_rank):
     nnz_train, nnz_test = int(trx.numel()), int(tex.numel())
     stream = torch.cuda.current_stream(dev)
     m = ft.FastTuckerPlus(tri, trx, A, B, precision=args.precision, scatter="hogwild",
-                          hot_rows=args.hot_rows, hot_window=args.hot_window)
+                          hot_rows=args.hot_rows, hot_window=args.hot_window, engine=args.engine)
 
     ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
 
@@ -339,7 +340,8 @@ def run_ours(args, rank, world, local_rank):
         "config": {
             "workload": args.workload if args.nnz is None else f"{args.workload} at {args.nnz} coordinates", "N": N, "I": list(w.I), "J": J, "R": R,
             "nnz_train": nnz_train, "nnz_test": nnz_test, "precision": args.precision,
-            "scatter": "hogwild", "hot_rows": m.cfg.hot_rows, "hot_window": m.cfg.hot_window,
+            "scatter": "hogwild", "engine": args.engine, "hot_rows": m.cfg.hot_rows,
+            "hot_window": m.cfg.hot_window,
             "lr_a": LR, "lr_b": LR_B, "lambda": LAM,
             "parallelism": "replicas" if world > 1 else "single",
             "l2": "inputs larger than L2 (training COO stream 1.2 GB per epoch)",
@@ -348,7 +350,8 @@ def run_ours(args, rank, world, local_rank):
                       "rmse": statistics.median(r_ms)},
         "test_rmse": last[0],
         "roofline": {
-            "bound": "hbm", "kernel": "k_factor", "achieved": achieved, "peak": peak,
+            "bound": "hbm", "kernel": "k_factor_tc" if args.engine == "tcgen05" else "k_factor",
+            "achieved": achieved, "peak": peak,
             "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
             "traffic": traffic, "bytes_per_nnz": per_nnz, "nnz_per_launch": nnz_train,
             "launch_ms": fac_ms,
@@ -364,6 +367,84 @@ def run_ours(args, rank, world, local_rank):
     if not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(args.cpu_sample)
     return out
+
+
+def time_phases(m, steps, warmup, stream):
+    """Median factor-pass and core-pass times (CUDA events) over `steps`
+    factor + core epochs after `warmup` untimed ones."""
+    for _ in range(warmup):
+        m.epoch_factors(LR, LAM)
+        m.epoch_core(LR_B, LAM)
+    torch.cuda.synchronize()
+    rec = []
+    for _ in range(steps):
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        e[0].record(stream)
+        m.epoch_factors(LR, LAM)
+        e[1].record(stream)
+        m.epoch_core(LR_B, LAM)
+        e[2].record(stream)
+        rec.append(e)
+    torch.cuda.synchronize()
+    f = statistics.median(a.elapsed_time(b) for a, b, _ in rec)
+    c = statistics.median(b.elapsed_time(c) for _, b, c in rec)
+    return f, c
+
+
+def engine_for(args, N, J, R):
+    """The requested factor-pass engine where it applies (tcgen05: BF16,
+    N <= 4, J, R <= 16), else the warp-tile kernels."""
+    ok = args.precision == "bf16" and N <= 4 and J <= 16 and R <= 16
+    return args.engine if ok else "warp"
+
+
+def run_sweep(args, local_rank):
+    """The paper's scaling studies on this GPU (Sec. 5): per-iteration factor
+    and core times (a) over the synthetic orders N = 3..10 (I = 10,000 per
+    mode, 1e8 uniform coordinates, J = R = 16) and (b) over (R, J) in
+    {16, 32}^2 on the Netflix-shaped Zipf tensor."""
+    dev = torch.device(f"cuda:{local_rank}")
+    torch.cuda.set_device(dev)
+    ft.load()
+    stream = torch.cuda.current_stream(dev)
+    peak, peak_kind = peak_hbm()
+    rows = []
+    if args.sweep in ("orders", "all"):
+        for N in range(3, 11):
+            w = synth.synthetic_order(N, nnz=args.nnz or 100_000_000)
+            w_, tri, trx, tei, tex, A, B = make_workload(dev, None, w)
+            eng = engine_for(args, N, 16, 16)
+            m = ft.FastTuckerPlus(tri, trx, A, B, precision=args.precision, hot_rows=args.hot_rows,
+                                  hot_window=args.hot_window, engine=eng)
+            f, c = time_phases(m, args.steps, args.warmup, stream)
+            nnz = int(trx.numel())
+            rmse = m.rmse(tei, tex)[0]
+            per = algorithmic_bytes_factor(N, w.J)
+            rows.append({"study": "order", "N": N, "I": w.I[0], "J": 16, "R": 16, "engine": eng, "nnz_train": nnz,
+                         "factor_ms": f, "core_ms": c, "value": nnz / ((f + c) / 1e3),
+                         "factor_frac_hbm": per * nnz / (f / 1e3) / 1e9 / peak, "test_rmse": rmse})
+            m.close()
+            del tri, trx, tei, tex, A, B
+            torch.cuda.empty_cache()
+    if args.sweep in ("ranks", "all"):
+        w0, tri, trx, tei, tex, _, _ = make_workload(dev, args.nnz, args.workload)
+        base = None
+        for R, J in ((16, 16), (16, 32), (32, 16), (32, 32)):
+            w = synth.Workload(**{**w0.__dict__, "J": (J,) * w0.N, "R": R})
+            A, B = synth.initial_factors(w, device=dev, mean_value=float(trx.double().mean()))
+            eng = engine_for(args, w0.N, J, R)
+            m = ft.FastTuckerPlus(tri, trx, A, B, precision=args.precision, hot_rows=args.hot_rows,
+                                  hot_window=args.hot_window, engine=eng)
+            f, c = time_phases(m, args.steps, args.warmup, stream)
+            nnz = int(trx.numel())
+            base = base or (f, c)
+            rows.append({"study": "rank", "workload": w0.name, "R": R, "J": J, "engine": eng, "nnz_train": nnz,
+                         "factor_ms": f, "core_ms": c, "factor_x": f / base[0], "core_x": c / base[1],
+                         "value": nnz / ((f + c) / 1e3)})
+            m.close()
+    return {"metric": METRIC, "unit": UNIT, "sweep": args.sweep, "precision": args.precision,
+            "steps": args.steps, "warmup": args.warmup, "peak_hbm_gbs": peak, "peak_kind": peak_kind,
+            "data": "synthetic", "rows": rows}
 
 
 def learned_step_ab(dev, epochs=20, lr=0.01, lam=0.01):
@@ -560,8 +641,14 @@ def main():
     ap.add_argument("--hot-rows", type=int, default=None,
                     help="rows per mode in the shared-memory hot-row cache (-1 auto, 0 off)")
     ap.add_argument("--hot-window", type=int, default=None, help="CTA tiles between cache write-backs")
+    ap.add_argument("--engine", choices=["warp", "tcgen05"], default="warp",
+                    help="factor-pass kernels: 16-nonzero warp tiles (mma.sync) or 128-nonzero "
+                         "warpgroup tiles (tcgen05.mma, TMEM)")
     ap.add_argument("--workload", default=WORKLOAD, choices=sorted(synth.WORKLOADS) + [BATCHED],
                     help="the timed tensor (default: the Netflix-shaped 1e8 Zipf tensor)")
+    ap.add_argument("--sweep", choices=["orders", "ranks", "all"], default=None,
+                    help="instead of the headline line: the order sweep N = 3..10 and/or the "
+                         "(R, J) sweep, per-iteration phase times")
     ap.add_argument("--nnz", type=int, default=None,
                     help="distinct coordinates drawn (default: the workload's 1e8); "
                          "a smaller case of the same recipe, e.g. for profiling")
@@ -579,6 +666,8 @@ def main():
     try:
         if args.impl == "reference":
             out = run_reference(args, rank, world)
+        elif args.sweep:
+            out = run_sweep(args, local_rank) if rank == 0 else None
         else:
             out = run_ours(args, rank, world, local_rank)
         if out is not None:

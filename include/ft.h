@@ -28,8 +28,8 @@
  *   - A^(n) is float32 row-major I_n x J_n; B^(n) is float32 row-major
  *     J_n x R.  Both are caller-owned, borrowed by the context, and updated
  *     in place by the epochs.
- *   - Supported shapes: 1 <= N <= 8, 1 <= J_n <= 32, 1 <= R <= 32, with
- *     N * K <= 160 where K = 16 if max(J_n, R) <= 16, else 32 (so N <= 8 at
+ *   - Supported shapes: 1 <= N <= 10, 1 <= J_n <= 32, 1 <= R <= 32, with
+ *     N * K <= 160 where K = 16 if max(J_n, R) <= 16, else 32 (so N <= 10 at
  *     K = 16 and N <= 5 at K = 32).  Others return FT_ERR_SHAPE.  nnz < 2^31.
  *   - The library allocates no device memory: all scratch lives in a
  *     caller-provided workspace (ft_workspace_size), 256-byte aligned.
@@ -51,7 +51,7 @@
 extern "C" {
 #endif
 
-#define FT_MAX_ORDER 8
+#define FT_MAX_ORDER 10
 #define FT_MAX_RANK 32
 
 typedef struct ft_ctx ft_ctx;
@@ -98,8 +98,16 @@ typedef struct {
   int hot_rows;
   int hot_window;      /* >= 1; default 64 */
   int hot_min_count;   /* >= 1; default 2 */
-  int reserved[4];     /* must be zero */
+  /* Kernel family of the Hogwild factor pass: FT_ENGINE_WARP (default) = one
+   * warp per 16-nonzero tile with mma.sync products; FT_ENGINE_TCGEN05 = one
+   * warpgroup per 128-nonzero tile, products on tcgen05.mma with TMEM
+   * accumulators (FT_BF16, J_n, R <= 16, N <= 4, FT_HOGWILD only; other
+   * configurations return FT_ERR_ARG from ft_workspace_size / ft_init). */
+  int engine;
+  int reserved[3];     /* must be zero */
 } ft_config;
+
+enum { FT_ENGINE_WARP = 0, FT_ENGINE_TCGEN05 = 1 };
 
 /* Fill *cfg with the defaults: FT_FP32, FT_HOGWILD, det_batch 4096, automatic
  * grid, hot_rows -1, hot_window 64, hot_min_count 2. */

@@ -29,7 +29,7 @@ UNITS = [("ft_api.cu", [], "ft_api"), ("ft_batch.cu", [], "ft_batch"), ("ft_step
 # the slowest units first, so a parallel build finishes early
 for _m in (0, 1, 2):
     for _k in (32, 16):
-        for _n in range(5 if _k == 32 else 8, 0, -1):
+        for _n in range(5 if _k == 32 else 10, 0, -1):
             UNITS.append(("ft_inst.cu", [f"-DFT_K={_k}", f"-DFT_MATH={_m}", f"-DFT_N={_n}"],
                           f"ft_inst_{_k}_{_m}_{_n}"))
 for _k in (16, 32):

@@ -7,7 +7,9 @@
 #include <cmath>
 #include <cstdint>
 #include <cstring>
+#include <map>
 #include <mutex>
+#include <utility>
 #include <new>
 #include <vector>
 
@@ -222,6 +224,7 @@ struct Plan {
   ft::KernelSet ks;
   ft::EvalSet es;
   int grid_factor = 0, grid_core = 0, grid_eval = 0;
+  int grid_factor_tc = 0;            // tcgen05 factor pass (engine FT_ENGINE_TCGEN05)
   int64_t det_S = 0, nbatches = 0;
   int hot_cap = 0;                   // cache slots, all modes (0 = no cache)
   size_t factor_smem = 0;            // Hogwild pass, tables + cache
@@ -239,10 +242,23 @@ constexpr size_t kMaxSmem = 227 * 1024;
 
 ft_status cuda_status(cudaError_t e) { return e == cudaSuccess ? FT_OK : FT_ERR_CUDA; }
 
+// The dynamic shared-memory limit is a property of the kernel function for
+// the whole process, so it is only ever raised: a context created later with
+// a smaller launch must not lower it under an older context's larger one.
 int occupancy(const void *fn, int threads, size_t smem) {
-  int nb = 0;
-  if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)) != cudaSuccess)
-    return 0;
+  static std::mutex mu;
+  static std::map<std::pair<int, const void *>, size_t> limit;   // (device, kernel)
+  int nb = 0, dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+  {
+    std::lock_guard<std::mutex> lock(mu);
+    size_t &lim = limit[std::make_pair(dev, fn)];
+    if (smem > lim) {
+      if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)) != cudaSuccess)
+        return 0;
+      lim = smem;
+    }
+  }
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, threads, smem) != cudaSuccess) return 0;
   return nb;
 }
@@ -261,8 +277,10 @@ ft_status make_plan(int N, const int64_t *I, const int *J, int R, int64_t nnz, c
   if (c.scatter == FT_DETERMINISTIC && c.det_batch < 1) return FT_ERR_ARG;
   if (c.blocks_per_sm < 0) return FT_ERR_ARG;
   if (c.hot_rows < -1 || c.hot_window < 1 || c.hot_min_count < 1) return FT_ERR_ARG;
-  for (int q = 0; q < 4; ++q)
+  for (int q = 0; q < 3; ++q)
     if (c.reserved[q] != 0) return FT_ERR_ARG;
+  if (c.engine != FT_ENGINE_WARP && c.engine != FT_ENGINE_TCGEN05) return FT_ERR_ARG;
+  if (c.engine == FT_ENGINE_TCGEN05 && (c.scatter != FT_HOGWILD || c.precision != FT_BF16)) return FT_ERR_ARG;
   int maxr = R;
   p->sumJ = 0;
   for (int n = 0; n < N; ++n) {
@@ -291,6 +309,9 @@ ft_status make_plan(int N, const int64_t *I, const int *J, int R, int64_t nnz, c
     return FT_ERR_CUDA;
   int64_t maxI = 1;
   for (int n = 0; n < N; ++n) maxI = std::max(maxI, I[n]);
+  const bool tc = c.engine == FT_ENGINE_TCGEN05;
+  if (tc && (K != 16 || p->ks.factor_tc == nullptr)) return FT_ERR_ARG;
+  const size_t factor_base_smem = tc ? p->ks.factor_tc_smem : p->ks.factor_smem;
   p->hot_cap = 0;
   if (c.scatter == FT_HOGWILD && c.hot_rows != 0 && nnz > 0) {
     const size_t per_slot = size_t(K) * sizeof(float) + 1;
@@ -298,14 +319,24 @@ ft_status make_plan(int N, const int64_t *I, const int *J, int R, int64_t nnz, c
     for (int n = 0; n < N; ++n) sumI += I[n];
     int64_t cap = c.hot_rows > 0 ? c.hot_rows : int64_t(kHotCacheBytes / per_slot);
     cap = std::min(cap, sumI);
-    const int64_t fit = int64_t((kMaxSmem - p->ks.factor_smem - 64) / per_slot);
+    const int64_t fit = int64_t((kMaxSmem - factor_base_smem - 64) / per_slot);
     if (cap > fit) return FT_ERR_ARG;
     p->hot_cap = int(std::max<int64_t>(cap, 0));
   }
-  p->factor_smem = p->ks.factor_smem + size_t(p->hot_cap) * K * sizeof(float) +
+  p->factor_smem = factor_base_smem + size_t(p->hot_cap) * K * sizeof(float) +
                    ((size_t(p->hot_cap) + 15) / 16) * 16;
   (void)maxI;
-  const int occ_f = occupancy(p->ks.factor, 256, p->factor_smem);
+  if (tc) {
+    // one CTA of 4 warpgroups per SM; the CTAs an SM can hold must not ask
+    // for more than its 512 TMEM columns (tcgen05.alloc would wait)
+    // (checked at the smallest launch, without the cache, where most fit)
+    const int occ_max = occupancy(p->ks.factor_tc, p->ks.factor_tc_threads, p->ks.factor_tc_smem);
+    const int occ_t = occupancy(p->ks.factor_tc, p->ks.factor_tc_threads, p->factor_smem);
+    const int per_sm = std::min(occ_t, c.blocks_per_sm ? c.blocks_per_sm : 1);
+    if (occ_t < 1 || occ_max * p->ks.factor_tc_tmem_cols > 512) return FT_ERR_CUDA;
+    p->grid_factor_tc = p->num_sms * per_sm;
+  }
+  const int occ_f = occupancy(p->ks.factor, 256, tc ? p->ks.factor_smem : p->factor_smem);
   const int occ_d = occupancy(p->ks.factor_delta, 256, p->ks.factor_smem);
   const int occ_c = occupancy(p->ks.core, p->ks.core_threads, p->ks.core_smem);
   const int occ_p = occupancy(p->es.predict, 256, p->es.smem);
@@ -545,6 +576,7 @@ ft_status take_error(ft_ctx *c, cudaStream_t st) {
   if (err == 0) return FT_OK;
   if (cudaMemsetAsync(d, 0, sizeof(int), st) != cudaSuccess) return FT_ERR_CUDA;
   if (err & ft::ERRBIT_INDEX) return FT_ERR_INDEX;
+  if (err & ft::ERRBIT_TIMEOUT) return FT_ERR_TIMEOUT;
   return FT_ERR_NONFINITE;
 }
 
@@ -653,6 +685,9 @@ ft_status ft_epoch_factors(ft_ctx *c, float lr_a, float lambda_a, const float *c
       a.hot_cap = p.hot_cap;
       a.hot_window = p.cfg.hot_window;
     }
+    if (p.cfg.engine == FT_ENGINE_TCGEN05)
+      return launch(c, p.ks.factor_tc, p.grid_factor_tc, p.ks.factor_tc_threads,
+                    c->hot_active ? p.factor_smem : p.ks.factor_tc_smem, &a, st);
     return launch(c, p.ks.factor, p.grid_factor, 256, c->hot_active ? p.factor_smem : p.ks.factor_smem,
                   &a, st);
   }

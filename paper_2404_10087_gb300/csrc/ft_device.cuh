@@ -21,7 +21,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
-#define FT_MAXN 8
+#define FT_MAXN 10
 #define FT_TILE 16
 
 // Cache path of the factor-phase row gathers (rows that other warps write
@@ -39,7 +39,7 @@ namespace ft {
 enum Math { MATH_FP32 = 0, MATH_TF32 = 1, MATH_BF16 = 2 };
 
 // Latched device error bits (workspace word 0).
-enum : int { ERRBIT_NONFINITE = 1, ERRBIT_INDEX = 2, ERRBIT_VALUE = 4 };
+enum : int { ERRBIT_NONFINITE = 1, ERRBIT_INDEX = 2, ERRBIT_VALUE = 4, ERRBIT_TIMEOUT = 8 };
 
 constexpr unsigned FULL = 0xffffffffu;
 

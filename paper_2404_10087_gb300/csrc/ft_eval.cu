@@ -35,6 +35,8 @@ bool FT_CAT(ft_eval, FT_K)(int N, ft::EvalSet *out) {
     case 6: *out = make_eval<6>(); return true;
     case 7: *out = make_eval<7>(); return true;
     case 8: *out = make_eval<8>(); return true;
+    case 9: *out = make_eval<9>(); return true;
+    case 10: *out = make_eval<10>(); return true;
 #endif
     default: return false;
   }

@@ -3,6 +3,9 @@
 // units compile in parallel.
 #include "ft_device.cuh"
 #include "ft_internal.h"
+#if FT_K == 16 && FT_MATH == 2
+#include "ft_tc05.cuh"
+#endif
 
 #ifndef FT_K
 #error "FT_K must be defined (16 or 32)"
@@ -38,6 +41,10 @@ ft::KernelSet make_set() {
     s.core = reinterpret_cast<const void *>(&ft::k_core_bf16r<N>);
     s.core_smem = ft::CoreRegSmem<N>::bytes();
     s.core_threads = 256;
+    s.factor_tc = reinterpret_cast<const void *>(&ft::k_factor_tc<N>);
+    s.factor_tc_smem = ft::tc::Smem<N>::bytes(0);
+    s.factor_tc_threads = ft::tc::THREADS;
+    s.factor_tc_tmem_cols = ft::tc::Smem<N>::TMEM_COLS;
   }
 #endif
   return s;

@@ -19,6 +19,11 @@ struct KernelSet {
   const void *batch_core = nullptr;
   size_t batch_core_smem = 0;
   int batch_core_threads = 256;
+  // tcgen05 Hogwild factor pass (BF16, K = 16, N <= 4), or null
+  const void *factor_tc = nullptr;
+  size_t factor_tc_smem = 0;           // without the hot-row cache
+  int factor_tc_threads = 0;
+  int factor_tc_tmem_cols = 0;         // TMEM columns one CTA allocates
 };
 
 // FP32 prediction / error / row-statistics kernels of one (N, K).
@@ -34,10 +39,10 @@ struct EvalSet {
 }  // namespace ft
 
 // One entry point per compiled instantiation unit (ft_inst.cu built with
-// FT_K in {16, 32}, FT_MATH in {0, 1, 2} and FT_N in 1..8 at K = 16, 1..5 at
+// FT_K in {16, 32}, FT_MATH in {0, 1, 2} and FT_N in 1..10 at K = 16, 1..5 at
 // K = 32; ft_eval.cu built with FT_K).
 #define FT_SETS_OF(X, K, M) X(K, M, 1) X(K, M, 2) X(K, M, 3) X(K, M, 4) X(K, M, 5)
-#define FT_SETS16(X, M) FT_SETS_OF(X, 16, M) X(16, M, 6) X(16, M, 7) X(16, M, 8)
+#define FT_SETS16(X, M) FT_SETS_OF(X, 16, M) X(16, M, 6) X(16, M, 7) X(16, M, 8) X(16, M, 9) X(16, M, 10)
 #define FT_ALL_SETS(X) \
   FT_SETS16(X, 0) FT_SETS16(X, 1) FT_SETS16(X, 2) FT_SETS_OF(X, 32, 0) FT_SETS_OF(X, 32, 1) FT_SETS_OF(X, 32, 2)
 #define FT_DECLARE_SET(K, M, N) bool ft_kernels_##K##_##M##_##N(ft::KernelSet *out);

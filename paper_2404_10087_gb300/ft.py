@@ -22,6 +22,8 @@ FT_FP32, FT_TF32, FT_BF16 = 0, 1, 2
 FT_HOGWILD, FT_DETERMINISTIC = 0, 1
 PRECISIONS = {"fp32": FT_FP32, "tf32": FT_TF32, "bf16": FT_BF16}
 SCATTERS = {"hogwild": FT_HOGWILD, "deterministic": FT_DETERMINISTIC}
+FT_ENGINE_WARP, FT_ENGINE_TCGEN05 = 0, 1
+ENGINES = {"warp": FT_ENGINE_WARP, "tcgen05": FT_ENGINE_TCGEN05}
 
 FT_OK = 0
 STATUS = {0: "FT_OK", -1: "FT_ERR_ARG", -2: "FT_ERR_INDEX", -3: "FT_ERR_SHAPE", -4: "FT_ERR_CUDA",
@@ -53,7 +55,7 @@ class ft_config(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("scatter", ctypes.c_int),
                 ("det_batch", ctypes.c_int64), ("blocks_per_sm", ctypes.c_int),
                 ("hot_rows", ctypes.c_int), ("hot_window", ctypes.c_int),
-                ("hot_min_count", ctypes.c_int), ("reserved", ctypes.c_int * 4)]
+                ("hot_min_count", ctypes.c_int), ("engine", ctypes.c_int), ("reserved", ctypes.c_int * 3)]
 
 
 _lib = None
@@ -136,7 +138,7 @@ def _stream(stream) -> int:
 
 
 def make_config(precision="fp32", scatter="hogwild", det_batch=4096, blocks_per_sm=0,
-                hot_rows=None, hot_window=None, hot_min_count=None) -> ft_config:
+                hot_rows=None, hot_window=None, hot_min_count=None, engine="warp") -> ft_config:
     c = ft_config()
     load().ft_config_default(ctypes.byref(c))
     c.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
@@ -149,6 +151,7 @@ def make_config(precision="fp32", scatter="hogwild", det_batch=4096, blocks_per_
         c.hot_window = int(hot_window)
     if hot_min_count is not None:
         c.hot_min_count = int(hot_min_count)
+    c.engine = ENGINES[engine] if isinstance(engine, str) else int(engine)
     return c
 
 
@@ -248,7 +251,8 @@ class FastTuckerPlus:
     """
 
     def __init__(self, idx, vals, A, B, precision="fp32", scatter="hogwild", det_batch=4096,
-                 blocks_per_sm=0, stream=None, hot_rows=None, hot_window=None, hot_min_count=None):
+                 blocks_per_sm=0, stream=None, hot_rows=None, hot_window=None, hot_min_count=None,
+                 engine="warp"):
         N = len(A)
         if not (len(idx) == len(B) == N):
             raise ValueError("idx, A and B need one entry per mode")
@@ -264,7 +268,7 @@ class FastTuckerPlus:
         self.R = int(B[0].shape[1])
         self.nnz = int(vals.numel())
         self.cfg = make_config(precision, scatter, det_batch, blocks_per_sm, hot_rows, hot_window,
-                               hot_min_count)
+                               hot_min_count, engine)
         ws = ft_workspace_size(self.I, self.J, self.R, self.nnz, self.cfg)
         self.workspace = torch.empty(max(ws, 256), dtype=torch.uint8, device=vals.device)
         self.ctx = ft_init(self.I, self.J, self.R, self.idx, vals, self.A, self.B, self.workspace,

@@ -192,6 +192,14 @@ WORKLOADS = {
 }
 
 
+
+def synthetic_order(N: int, nnz: int = 100_000_000) -> Workload:
+    """The paper's synthetic family (Sec. 5.1, synthetic dataset table):
+    order N in 3..10, every mode of size 10,000, 1e8 uniform coordinates,
+    integer values 1..5 (here: a planted J = R = 16 model mapped to ratings)."""
+    return Workload(name=f"synthetic_order{N}_1e8", I=(10_000,) * N, nnz=nnz, J=(16,) * N, R=16,
+                    dist="uniform", planted_std=0.25, ratings=True)
+
 @dataclass
 class Draw:
     """The random part of a workload: coordinates, planted model, noise, split."""
@@ -239,19 +247,27 @@ def initial_factors(w: Workload, device="cpu", mean_value: float | None = None, 
     return A, B
 
 
-def random_problem(seed: int, I, J, R, nnz, device="cpu", std=None, value_std=1.0):
+def random_problem(seed: int, I, J, R, nnz, device="cpu", std=None, value_std=1.0, positive=False):
     """A small unstructured problem for parity tests: uniform coordinates
     (duplicates allowed), N(0, s_n^2) factors and cores, N(0, value_std^2)
     values.  By default s_n = (R^(-1/N) / J_n)^(1/4), which makes every
     a^(n) B^(n) entry of variance R^(-1/N) and the prediction of variance
-    about 1, so SGD steps stay well scaled for any N, J, R."""
+    about 1, so SGD steps stay well scaled for any N, J, R.  positive=True
+    takes the absolute values of the factor and core draws (no cancellation
+    in the products a.B)."""
     gen = generator(seed, device)
     N = len(I)
     idx = torch.stack([torch.randint(0, int(In), (nnz,), generator=gen, device=device)
                        for In in I]).to(torch.int32)
-    sd = [std if std is not None else (R ** (-1.0 / N) / Jn) ** 0.25 for Jn in J]
+    if positive:   # |N(0, s^2)| has mean s sqrt(2/pi): mean of every a.B entry R^(-1/N)
+        sd = [std if std is not None else math.sqrt(math.pi / 2 * R ** (-1.0 / N) / Jn) for Jn in J]
+    else:
+        sd = [std if std is not None else (R ** (-1.0 / N) / Jn) ** 0.25 for Jn in J]
     A = [normal_matrices(gen, [(In, Jn)], s, device)[0] for In, Jn, s in zip(I, J, sd)]
     B = [normal_matrices(gen, [(Jn, R)], s, device)[0] for Jn, s in zip(J, sd)]
+    if positive:
+        A = [a.abs() for a in A]
+        B = [b.abs() for b in B]
     x = (torch.randn(nnz, generator=gen, device=device, dtype=torch.float64) * value_std).to(torch.float32)
     return idx, x, A, B
 

@@ -52,7 +52,8 @@ def test_host_only_calls_without_gpu():
 def test_shape_rejection_before_any_device_call():
     """Unsupported shapes are refused on the host (no device query needed)."""
     cfg = ft.make_config()
-    for I, J, R in [((10,) * 9, (4,) * 9, 4),       # N > 8
+    for I, J, R in [((10,) * 11, (4,) * 11, 4),     # N > 10
+                    ((10,) * 6, (17,) * 6, 4),       # N > 5 at K = 32
                     ((10, 10), (4, 33), 4),          # J > 32
                     ((10, 10), (4, 4), 33),          # R > 32
                     ((10,) * 6, (32,) * 6, 8),       # N * K > 160
@@ -60,3 +61,15 @@ def test_shape_rejection_before_any_device_call():
         with pytest.raises(ft.FtError) as e:
             ft.ft_workspace_size(I, J, R, 100, cfg)
         assert e.value.status == -3
+
+
+def test_engine_configuration_rejected_on_host():
+    """The tcgen05 engine is BF16 Hogwild only; unknown engines are refused."""
+    I, J, R = (10, 10, 10), (16, 16, 16), 16
+    for kw in (dict(precision="fp32", engine="tcgen05"), dict(precision="tf32", engine="tcgen05"),
+               dict(precision="bf16", scatter="deterministic", engine="tcgen05"),
+               dict(precision="bf16", engine=7)):
+        cfg = ft.make_config(**kw)
+        with pytest.raises(ft.FtError) as e:
+            ft.ft_workspace_size(I, J, R, 100, cfg)
+        assert e.value.status == -1, kw

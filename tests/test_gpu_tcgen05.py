@@ -1,0 +1,166 @@
+"""The tcgen05 factor pass (FT_ENGINE_TCGEN05: 128-nonzero warpgroup tiles,
+products on tcgen05.mma with TMEM accumulators) against the FP64 oracle,
+through the C ABI.
+
+Tolerances as for the BF16 warp-tile pass: one epoch's step A_new - A_old
+within 2e-2 (Frobenius, relative) of the oracle's when no two nonzeros share
+a row (no races, so the Hogwild pass equals the sequential epoch).  Sizes
+span several 128-nonzero tiles, several CTAs and a ragged tail.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2404_10087_gb300 import ft, synth
+
+pytestmark = pytest.mark.gpu
+
+DEV = "cuda:0"
+TOL = 2e-2
+
+
+def f64(ts):
+    return [t.detach().double().cpu().numpy() for t in ts]
+
+
+def rel_fro(got, ref):
+    d = np.linalg.norm(ref)
+    return float(np.linalg.norm(got - ref) / d) if d > 0 else float(np.linalg.norm(got))
+
+
+def distinct_rows_problem(seed, nnz, J, R, extra=7):
+    """nnz nonzeros whose rows are distinct in every mode."""
+    N = len(J)
+    I = tuple(nnz + extra * (n + 1) for n in range(N))
+    g = torch.Generator().manual_seed(seed)
+    idx = torch.stack([torch.randperm(In, generator=g)[:nnz] for In in I]).to(torch.int32)
+    _, x, A, B = synth.random_problem(seed, I, J, R, nnz)
+    return I, idx, x, A, B
+
+
+SHAPES = [
+    ((16, 16, 16), 16, 128 * 40 + 77),       # the Netflix-shaped ranks, ragged tail
+    ((16, 16, 16), 16, 128 * 4 * 152 * 2 + 5),  # more tiles than one pass of the grid
+    ((4, 12, 9), 13, 1000),                  # J, R below 16 (zero padding, scalar rows)
+    ((16, 8), 16, 700),
+    ((16,), 11, 300),
+    ((16, 16, 12, 8), 16, 2000),
+]
+IDS = [f"N{len(s[0])}_J{max(s[0])}_R{s[1]}_nnz{s[2]}" for s in SHAPES]
+
+
+@pytest.mark.parametrize("cache", [dict(hot_rows=0), dict(hot_min_count=1), dict(hot_min_count=1, hot_window=1)],
+                         ids=["no_cache", "all_rows_cacheable", "window_1"])
+@pytest.mark.parametrize("shape", SHAPES, ids=IDS)
+def test_collision_free_epoch_matches_oracle(shape, cache):
+    J, R, nnz = shape
+    I, idx, x, A, B = distinct_rows_problem(11, nnz, J, R)
+    gidx = [idx[n].contiguous().to(DEV) for n in range(len(J))]
+    gA = [a.clone().to(DEV) for a in A]
+    gB = [b.clone().to(DEV) for b in B]
+    m = ft.FastTuckerPlus(gidx, x.to(DEV), gA, gB, precision="bf16", engine="tcgen05", **cache)
+    m.epoch_factors(0.03, 0.02)
+    m.check()
+    ref = oracle.factor_epoch(f64(A), f64(B), idx.numpy(), x.double().numpy(), 1, 0.03, 0.02)
+    got = f64(gA)
+    for n in range(len(J)):
+        assert rel_fro(got[n] - f64(A)[n], ref[n] - f64(A)[n]) <= TOL, n
+    # B is not touched by the factor pass
+    for b0, b in zip(B, gB):
+        assert torch.equal(b0, b.cpu())
+
+
+def test_row_step_scale():
+    J, R, nnz = (16, 16, 16), 16, 3000
+    I, idx, x, A, B = distinct_rows_problem(12, nnz, J, R)
+    g = torch.Generator().manual_seed(4)
+    scales = [torch.rand(In, generator=g) * 3.75 + 0.25 for In in I]
+    gidx = [idx[n].contiguous().to(DEV) for n in range(3)]
+    gA = [a.clone().to(DEV) for a in A]
+    m = ft.FastTuckerPlus(gidx, x.to(DEV), gA, [b.to(DEV) for b in B], precision="bf16", engine="tcgen05")
+    m.epoch_factors(0.02, 0.01, [s.to(DEV) for s in scales])
+    m.check()
+    ref = oracle.factor_epoch(f64(A), f64(B), idx.numpy(), x.double().numpy(), 1, 0.02, 0.01,
+                              row_scale=[s.double().numpy() for s in scales])
+    for n in range(3):
+        assert rel_fro(f64(gA)[n] - f64(A)[n], ref[n] - f64(A)[n]) <= TOL
+
+
+def test_agrees_with_warp_engine():
+    """Both engines compute the same BF16 products with FP32 accumulation:
+    on a collision-free epoch they agree far inside the oracle tolerance."""
+    J, R, nnz = (16, 16, 16), 16, 5000
+    I, idx, x, A, B = distinct_rows_problem(13, nnz, J, R)
+    outs = []
+    for engine in ("warp", "tcgen05"):
+        gA = [a.clone().to(DEV) for a in A]
+        m = ft.FastTuckerPlus([idx[n].contiguous().to(DEV) for n in range(3)], x.to(DEV), gA,
+                              [b.to(DEV) for b in B], precision="bf16", engine=engine, hot_rows=0)
+        m.epoch_factors(0.03, 0.02)
+        m.check()
+        outs.append(f64(gA))
+    for n in range(3):
+        step_w, step_t = outs[0][n] - f64(A)[n], outs[1][n] - f64(A)[n]
+        assert rel_fro(step_t, step_w) <= 2e-3, n
+
+
+def test_hogwild_training_converges():
+    """Ten Hogwild epochs on the planted 3-order workload (1e5 uniform
+    coordinates on 1000 rows per mode, so many updates collide inside a
+    128-nonzero tile): the test RMSE falls and stays within 35% of the
+    sequential FP64 oracle's."""
+    w = synth.WORKLOADS["planted_uniform_1e5"]
+    d = synth.draw_workload(w)
+    planted = oracle.predict(f64(d.planted_A), f64(d.planted_B), d.idx.numpy())
+    x = (torch.from_numpy(planted) + d.noise.double()).float()
+    A0, B0 = synth.initial_factors(w)
+    tr, te = d.train, d.test
+    gA = [a.clone().to(DEV) for a in A0]
+    gB = [b.clone().to(DEV) for b in B0]
+    tri = [d.idx[n, tr].contiguous().to(DEV) for n in range(3)]
+    tei = [d.idx[n, te].contiguous().to(DEV) for n in range(3)]
+    m = ft.FastTuckerPlus(tri, x[tr].contiguous().to(DEV), gA, gB, precision="bf16", engine="tcgen05")
+    lr = lam = 0.01
+    oA, oB = f64(A0), f64(B0)
+    itr, ite = d.idx[:, tr].numpy(), d.idx[:, te].numpy()
+    xtr, xte = x[tr].double().numpy(), x[te].double().numpy()
+    r0 = oracle.errors(oA, oB, ite, xte)[0]
+    for _ in range(10):
+        m.epoch_factors(lr, lam)
+        m.epoch_core(lr, lam)
+        oA = oracle.factor_epoch(oA, oB, itr, xtr, 1, lr, lam)
+        oB = oracle.core_epoch(oA, oB, itr, xtr, lr, lam, nthreads=oracle.default_threads())
+    g = m.rmse(tei, x[te].contiguous().to(DEV))[0]
+    o = oracle.errors(oA, oB, ite, xte)[0]
+    assert g < r0, (g, r0)
+    assert g <= 1.35 * o, (g, o)
+
+
+def test_bad_index_is_reported_and_masked():
+    J, R, nnz = (16, 16, 16), 16, 600
+    I, idx, x, A, B = distinct_rows_problem(14, nnz, J, R)
+    gidx = [idx[n].contiguous().to(DEV) for n in range(3)]
+    gA = [a.clone().to(DEV) for a in A]
+    m = ft.FastTuckerPlus(gidx, x.to(DEV), gA, [b.to(DEV) for b in B], precision="bf16", engine="tcgen05",
+                          hot_rows=0)
+    gidx[1][17] = I[1] + 3      # out of range after ft_init validated the tensor
+    m.epoch_factors(0.03, 0.02)
+    with pytest.raises(ft.FtError) as e:
+        m.check()
+    assert e.value.status == -2
+    m.close()
+
+
+def test_empty_and_single_nonzero():
+    for nnz in (0, 1):
+        J, R = (16, 16, 16), 16
+        I, idx, x, A, B = distinct_rows_problem(15, nnz, J, R)
+        gA = [a.clone().to(DEV) for a in A]
+        m = ft.FastTuckerPlus([idx[n].contiguous().to(DEV) for n in range(3)], x.to(DEV), gA,
+                              [b.to(DEV) for b in B], precision="bf16", engine="tcgen05")
+        m.epoch_factors(0.03, 0.02)
+        m.check()
+        ref = oracle.factor_epoch(f64(A), f64(B), idx.numpy(), x.double().numpy(), 1, 0.03, 0.02)
+        for n in range(3):
+            np.testing.assert_allclose(f64(gA)[n], ref[n], rtol=0, atol=2e-2 * max(1e-30, np.abs(ref[n]).max()))
