@@ -69,9 +69,12 @@ def kernel_digest():
     return h.hexdigest()[:16]
 
 
-def recorded_traffic(precision):
+def recorded_traffic(precision, workload=WORKLOAD, nnz=None, engine="warp"):
     """DRAM bytes per factor launch from the committed ncu summary, if it was
-    taken on the current kernel source; else None."""
+    taken on the current kernel source and on this launch (the default
+    workload at full size, warp-tile engine); else None."""
+    if workload != WORKLOAD or nnz is not None or engine != "warp":
+        return None
     p = os.path.join(ROOT, "profiles", "ncu_factor_netflix_zipf.md")
     if not os.path.exists(p):
         return None
@@ -319,10 +322,11 @@ def run_ours(args, rank, world, local_rank):
         return None
 
     per_nnz = algorithmic_bytes_factor(N, J)
+    coo_bytes = (4 * N + 4) * nnz_train
     fac_ms = statistics.mean(f_ms)
     achieved = per_nnz * nnz_train / (fac_ms / 1e3) / 1e9
     peak, peak_kind = peak_hbm()
-    traffic = recorded_traffic(args.precision)
+    traffic = recorded_traffic(args.precision, args.workload, args.nnz, args.engine)
     clocks = clk.summary()
     out = {
         "metric": METRIC,
@@ -344,7 +348,7 @@ def run_ours(args, rank, world, local_rank):
             "hot_window": m.cfg.hot_window,
             "lr_a": LR, "lr_b": LR_B, "lambda": LAM,
             "parallelism": "replicas" if world > 1 else "single",
-            "l2": "inputs larger than L2 (training COO stream 1.2 GB per epoch)",
+            "l2": f"inputs larger than L2 (training COO stream {coo_bytes / 1e9:.2f} GB per epoch)",
         },
         "phases_ms": {"factor": statistics.median(f_ms), "core": statistics.median(c_ms),
                       "rmse": statistics.median(r_ms)},

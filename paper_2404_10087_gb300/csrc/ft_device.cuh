@@ -811,8 +811,9 @@ __global__ void __launch_bounds__(256) k_core(const EpochArgs p) {
 }
 
 // ------------------------------------------- core phase, BF16 in registers
-// The same core-gradient pass (Algorithm 5) for K = 16 with BF16 tensor
-// cores, arranged so that nothing is staged through shared memory:
+// Tile arithmetic of the core-gradient pass (Algorithm 5) for K = 16 with
+// BF16 tensor cores (core16_tile), arranged so that no operand of the
+// products is staged through shared memory:
 //   * C^T = B^T A_Psi^T (mma m16n8k16, M = r, N = the tile's 16 nonzeros,
 //     K = j): the gathered rows, packed to bf16, are already the B operand,
 //     and the accumulator (rows r = g, g + 8; columns m = 2t, 2t + 1 of each
@@ -847,13 +848,10 @@ struct CoreRegSmem {
   static constexpr size_t bytes() { return sizeof(uint32_t) * (size_t(N) * TABW) + sizeof(float) * N * ACC; }
 };
 
+// B^T as the A operand of C^T = B^T A_Psi^T, one table per mode: register q of
+// lane (g, t) holds rows r = g + 8 (q & 1), logical k = 2t + 8 (q >> 1) + {0, 1}.
 template <int N>
-__global__ void __launch_bounds__(256) k_core_bf16r(const EpochArgs p) {
-  extern __shared__ __align__(16) float smem[];
-  uint32_t *tab = reinterpret_cast<uint32_t *>(smem);      // [N][4][32]
-  float *cacc = smem + N * CoreRegSmem<N>::TABW;            // [N][2][8][32]
-  // B^T as the A operand: reg q of lane (g, t) holds rows r = g + 8 (q & 1),
-  // logical k = 2t + 8 (q >> 1) + {0, 1}
+__device__ __forceinline__ void core16_setup(const EpochArgs &p, uint32_t *tab, float *cacc) {
   for (int e = threadIdx.x; e < N * 128; e += blockDim.x) {
     const int n = e >> 7, q = (e >> 5) & 3, lane = e & 31;
     const int g = lane >> 2, t = lane & 3;
@@ -865,133 +863,83 @@ __global__ void __launch_bounds__(256) k_core_bf16r(const EpochArgs p) {
     tab[e] = pack_bf16(v0, v1);
   }
   for (int e = threadIdx.x; e < N * CoreRegSmem<N>::ACC; e += blockDim.x) cacc[e] = 0.f;
-  __syncthreads();
+}
 
-  const int lane = threadIdx.x & 31;
-  const int g = lane >> 2, t = lane & 3;
-  float gs[N][8], gc[N][8];
+// One tile of the register-resident core pass.  ab[n][u]: the lane's chunk of
+// the mode-n row of nonzero base + 8u + g, packed to bf16 (zeros for a masked
+// nonzero); xv[u][q]: the value of nonzero base + 8u + 2t + q.  Adds the
+// tile's G^T into the lane's Neumaier registers (gs, gc).
+template <int N>
+__device__ __forceinline__ void core16_tile(const EpochArgs &p, const uint32_t *tab, const uint32_t (&ab)[N][2][2],
+                                            const float (&xv)[2][2], int64_t base, float (&gs)[N][8],
+                                            float (&gc)[N][8], int lane) {
+  const int t = lane & 3;
+  // C^T per mode: ct[n][u][i], rows r = g + 8 (i >> 1), column m = 8u + 2t + (i & 1)
+  float ct[N][2][4];
 #pragma unroll
-  for (int n = 0; n < N; ++n)
-#pragma unroll
-    for (int i = 0; i < 8; ++i) gs[n][i] = gc[n][i] = 0.f;
-
-  const int64_t warp = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
-  const int64_t nwarps = (int64_t(gridDim.x) * blockDim.x) >> 5;
-  const int64_t ntiles = (p.end - p.begin + FT_TILE - 1) / FT_TILE;
-  // coordinates of rows m = base + g (u = 0) and base + 8 + g (u = 1), and the
-  // values of the lane's columns m = base + 8u + 2t + q, loaded a tile ahead
-  int32_t nrow[N][2];
-  float nxv[2][2];
-  auto load_coords = [&](int64_t tile) {
-    const int64_t b = p.begin + tile * FT_TILE;
-#pragma unroll
-    for (int u = 0; u < 2; ++u)
-#pragma unroll
-      for (int n = 0; n < N; ++n) nrow[n][u] = (b + 8 * u + g < p.end) ? __ldcs(p.idx[n] + b + 8 * u + g) : 0;
-#pragma unroll
-    for (int u = 0; u < 2; ++u)
-#pragma unroll
-      for (int q = 0; q < 2; ++q) {
-        const int64_t m = b + 8 * u + 2 * t + q;
-        nxv[u][q] = m < p.end ? __ldcs(p.vals + m) : 0.f;
-      }
-  };
-  if (warp < ntiles) load_coords(warp);
-  for (int64_t tile = warp; tile < ntiles; tile += nwarps) {
-    const int64_t base = p.begin + tile * FT_TILE;
-    int32_t row[N][2];
-    float xv[2][2];
-    bool valid[2];
+  for (int n = 0; n < N; ++n) {
+    const uint32_t a0 = tab[(n * 4 + 0) * 32 + lane], a1 = tab[(n * 4 + 1) * 32 + lane];
+    const uint32_t a2 = tab[(n * 4 + 2) * 32 + lane], a3 = tab[(n * 4 + 3) * 32 + lane];
 #pragma unroll
     for (int u = 0; u < 2; ++u) {
-      valid[u] = base + 8 * u + g < p.end;
+      float acc[4] = {0.f, 0.f, 0.f, 0.f};
+      mma_bf16(acc, a0, a1, a2, a3, ab[n][u][0], ab[n][u][1]);
 #pragma unroll
-      for (int n = 0; n < N; ++n) row[n][u] = nrow[n][u];
-#pragma unroll
-      for (int q = 0; q < 2; ++q) xv[u][q] = nxv[u][q];
-    }
-    if (tile + nwarps < ntiles) load_coords(tile + nwarps);
-    bool bad = false;
-#pragma unroll
-    for (int u = 0; u < 2; ++u) {
-      bool ok = true;
-#pragma unroll
-      for (int n = 0; n < N; ++n) ok = ok && row[n][u] >= 0 && int64_t(row[n][u]) < p.I[n];
-      if (valid[u] && !ok) { bad = true; valid[u] = false; }
-    }
-    if (bad) atomicOr(p.err, ERRBIT_INDEX);
-    // the rows, packed to bf16
-    uint32_t ab[N][2][2];
-#pragma unroll
-    for (int n = 0; n < N; ++n)
-#pragma unroll
-      for (int u = 0; u < 2; ++u) {
-        float v[4];
-        load_chunk<16, true>(p.A[n], row[n][u], p.J[n], t, valid[u], (p.vecmask >> n) & 1, v);
-        ab[n][u][0] = pack_bf16(v[0], v[1]);
-        ab[n][u][1] = pack_bf16(v[2], v[3]);
-      }
-    // C^T per mode: ct[n][u][i], rows r = g + 8 (i >> 1), column m = 8u + 2t + (i & 1)
-    float ct[N][2][4];
-#pragma unroll
-    for (int n = 0; n < N; ++n) {
-      const uint32_t a0 = tab[(n * 4 + 0) * 32 + lane], a1 = tab[(n * 4 + 1) * 32 + lane];
-      const uint32_t a2 = tab[(n * 4 + 2) * 32 + lane], a3 = tab[(n * 4 + 3) * 32 + lane];
-#pragma unroll
-      for (int u = 0; u < 2; ++u) {
-        float acc[4] = {0.f, 0.f, 0.f, 0.f};
-        mma_bf16(acc, a0, a1, a2, a3, ab[n][u][0], ab[n][u][1]);
-#pragma unroll
-        for (int i = 0; i < 4; ++i) ct[n][u][i] = acc[i];
-      }
-    }
-    // xhat of the lane's nonzeros m = 8u + 2t + q, then (xhat - x)
-    float ne[2][2];
-#pragma unroll
-    for (int u = 0; u < 2; ++u)
-#pragma unroll
-      for (int q = 0; q < 2; ++q) {
-        float s0 = 1.f, s1 = 1.f;
-#pragma unroll
-        for (int n = 0; n < N; ++n) { s0 *= ct[n][u][q]; s1 *= ct[n][u][q + 2]; }
-        float sum = s0 + s1;
-        sum += __shfl_xor_sync(FULL, sum, 4);
-        sum += __shfl_xor_sync(FULL, sum, 8);
-        sum += __shfl_xor_sync(FULL, sum, 16);
-        const int64_t m = base + 8 * u + 2 * t + q;
-        ne[u][q] = m < p.end ? sum - xv[u][q] : 0.f;
-      }
-    const bool nonfinite = !isfinite(ne[0][0]) || !isfinite(ne[0][1]) || !isfinite(ne[1][0]) || !isfinite(ne[1][1]);
-    if (__any_sync(FULL, nonfinite) && lane == 0) atomicOr(p.err, ERRBIT_NONFINITE);
-#pragma unroll
-    for (int n = 0; n < N; ++n) {
-      // D^T as the A operand (k = the nonzeros)
-      float d[2][4];
-#pragma unroll
-      for (int u = 0; u < 2; ++u)
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-          float pr = 1.f;
-#pragma unroll
-          for (int k = 0; k < N; ++k)
-            if (k != n) pr *= ct[k][u][i];
-          d[u][i] = pr;
-        }
-      const uint32_t da0 = pack_bf16(d[0][0], d[0][1]), da1 = pack_bf16(d[0][2], d[0][3]);
-      const uint32_t da2 = pack_bf16(d[1][0], d[1][1]), da3 = pack_bf16(d[1][2], d[1][3]);
-#pragma unroll
-      for (int v = 0; v < 2; ++v) {
-        // E (k = nonzeros, n = logical j = 8v + g)
-        const uint32_t e0 = scale_bf16x2(movmatrix_trans(ab[n][0][v]), ne[0][0], ne[0][1]);
-        const uint32_t e1 = scale_bf16x2(movmatrix_trans(ab[n][1][v]), ne[1][0], ne[1][1]);
-        float acc[4] = {0.f, 0.f, 0.f, 0.f};
-        mma_bf16(acc, da0, da1, da2, da3, e0, e1);
-#pragma unroll
-        for (int i = 0; i < 4; ++i) neumaier_add(gs[n][4 * v + i], gc[n][4 * v + i], acc[i]);
-      }
+      for (int i = 0; i < 4; ++i) ct[n][u][i] = acc[i];
     }
   }
-  // CTA combine in warp order, then the CTA partial in the [n][K][K] layout
+  // xhat of the lane's nonzeros m = 8u + 2t + q, then (xhat - x)
+  float ne[2][2];
+#pragma unroll
+  for (int u = 0; u < 2; ++u)
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      float s0 = 1.f, s1 = 1.f;
+#pragma unroll
+      for (int n = 0; n < N; ++n) { s0 *= ct[n][u][q]; s1 *= ct[n][u][q + 2]; }
+      float sum = s0 + s1;
+      sum += __shfl_xor_sync(FULL, sum, 4);
+      sum += __shfl_xor_sync(FULL, sum, 8);
+      sum += __shfl_xor_sync(FULL, sum, 16);
+      const int64_t m = base + 8 * u + 2 * t + q;
+      ne[u][q] = m < p.end ? sum - xv[u][q] : 0.f;
+    }
+  const bool nonfinite = !isfinite(ne[0][0]) || !isfinite(ne[0][1]) || !isfinite(ne[1][0]) || !isfinite(ne[1][1]);
+  if (__any_sync(FULL, nonfinite) && lane == 0) atomicOr(p.err, ERRBIT_NONFINITE);
+#pragma unroll
+  for (int n = 0; n < N; ++n) {
+    // D^T as the A operand (k = the nonzeros)
+    float d[2][4];
+#pragma unroll
+    for (int u = 0; u < 2; ++u)
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        float pr = 1.f;
+#pragma unroll
+        for (int k = 0; k < N; ++k)
+          if (k != n) pr *= ct[k][u][i];
+        d[u][i] = pr;
+      }
+    const uint32_t da0 = pack_bf16(d[0][0], d[0][1]), da1 = pack_bf16(d[0][2], d[0][3]);
+    const uint32_t da2 = pack_bf16(d[1][0], d[1][1]), da3 = pack_bf16(d[1][2], d[1][3]);
+#pragma unroll
+    for (int v = 0; v < 2; ++v) {
+      // E (k = nonzeros, n = logical j = 8v + g)
+      const uint32_t e0 = scale_bf16x2(movmatrix_trans(ab[n][0][v]), ne[0][0], ne[0][1]);
+      const uint32_t e1 = scale_bf16x2(movmatrix_trans(ab[n][1][v]), ne[1][0], ne[1][1]);
+      float acc[4] = {0.f, 0.f, 0.f, 0.f};
+      mma_bf16(acc, da0, da1, da2, da3, e0, e1);
+#pragma unroll
+      for (int i = 0; i < 4; ++i) neumaier_add(gs[n][4 * v + i], gc[n][4 * v + i], acc[i]);
+    }
+  }
+}
+
+// CTA combine of the lanes' Neumaier registers in warp order, then the CTA
+// partial in the [n][K][K] layout of (sum, compensation) pairs.
+template <int N>
+__device__ __forceinline__ void core16_combine(const EpochArgs &p, float *cacc, const float (&gs)[N][8],
+                                               const float (&gc)[N][8], int lane) {
   const int w = threadIdx.x >> 5, nw = blockDim.x >> 5;
   for (int ww = 0; ww < nw; ++ww) {
     if (w == ww) {
@@ -1024,6 +972,327 @@ __global__ void __launch_bounds__(256) k_core_bf16r(const EpochArgs p) {
     const size_t o = (size_t(n) * 16 + j) * 16 + r;
     out[2 * o] = cacc[((n * 2 + 0) * 8 + i) * 32 + ln];
     out[2 * o + 1] = cacc[((n * 2 + 1) * 8 + i) * 32 + ln];
+  }
+}
+
+// ------------------------------- core phase, BF16 in registers, pipelined
+// The tile arithmetic above (core16_tile) with the row gathers moved off the
+// critical path of the warp: each warp keeps
+// a ring of CORE_STAGES tile buffers in shared memory and fills the buffer of
+// tile k + CORE_STAGES - 1 with asynchronous copies (cp.async, through L1)
+// while it computes tile k, so that every gather has CORE_STAGES - 1 tiles of
+// work to arrive instead of none.  A lane copies and later reads only its
+// own 16-byte chunk of each row; the tile's 16 values are copied by lanes
+// 0..15 and read by every lane after a warp barrier.  Masked nonzeros (past
+// the end, or with a coordinate outside [0, I_n), which latches
+// ERRBIT_INDEX) get zero-filled rows and values.
+constexpr int CORE_STAGES = 3;
+
+template <int N>
+struct CorePipeSmem {
+  static constexpr int ROWS = N * 2 * 32 * 16;         // bytes of one stage's rows: [n][u][lane] x 16 B
+  static constexpr int STAGE = ROWS + FT_TILE * 4;      // + the tile's values
+  static constexpr int WARP = CORE_STAGES * STAGE;
+  static constexpr int BASE = 4 * N * (CoreRegSmem<N>::TABW + CoreRegSmem<N>::ACC);  // tables, CTA sums
+  static constexpr size_t bytes(int warps) { return size_t(BASE) + size_t(warps) * WARP; }
+};
+
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void *src, int src_bytes) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(src_bytes) : "memory");
+}
+__device__ __forceinline__ void cp_async4(uint32_t dst, const void *src, int src_bytes) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(dst), "l"(src), "r"(src_bytes) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int PENDING>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(PENDING) : "memory");
+}
+
+template <int N>
+__global__ void __launch_bounds__(256, N <= 3 ? 2 : 1) k_core_bf16p(const EpochArgs p) {
+  using L = CorePipeSmem<N>;
+  extern __shared__ __align__(16) float smem[];
+  uint32_t *tab = reinterpret_cast<uint32_t *>(smem);      // [N][4][32]
+  float *cacc = smem + N * CoreRegSmem<N>::TABW;            // [N][2][8][32]
+  core16_setup<N>(p, tab, cacc);
+  const int lane = threadIdx.x & 31;
+  const int g = lane >> 2, t = lane & 3;
+  unsigned char *ring = reinterpret_cast<unsigned char *>(smem) + L::BASE + (threadIdx.x >> 5) * L::WARP;
+  const uint32_t ring_s = static_cast<uint32_t>(__cvta_generic_to_shared(ring));
+  __syncthreads();
+
+  float gs[N][8], gc[N][8];
+#pragma unroll
+  for (int n = 0; n < N; ++n)
+#pragma unroll
+    for (int i = 0; i < 8; ++i) gs[n][i] = gc[n][i] = 0.f;
+
+  const int64_t warp = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = (int64_t(gridDim.x) * blockDim.x) >> 5;
+  const int64_t ntiles = (p.end - p.begin + FT_TILE - 1) / FT_TILE;
+
+  // coordinates of the next tile to fetch: rows m = base + 8u + g
+  int32_t nrow[N][2];
+  auto load_coords = [&](int64_t tile) {
+    const int64_t b = p.begin + tile * FT_TILE;
+#pragma unroll
+    for (int u = 0; u < 2; ++u)
+#pragma unroll
+      for (int n = 0; n < N; ++n) nrow[n][u] = (b + 8 * u + g < p.end) ? __ldcs(p.idx[n] + b + 8 * u + g) : 0;
+  };
+  // asynchronous copies of tile `tile` (coordinates in nrow) into ring stage s
+  auto fetch = [&](int64_t tile, int s) {
+    const int64_t b = p.begin + tile * FT_TILE;
+    const uint32_t st = ring_s + uint32_t(s * L::STAGE);
+    bool valid[2], bad = false;
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      valid[u] = b + 8 * u + g < p.end;
+      bool ok = true;
+#pragma unroll
+      for (int n = 0; n < N; ++n) ok = ok && nrow[n][u] >= 0 && int64_t(nrow[n][u]) < p.I[n];
+      if (valid[u] && !ok) { bad = true; valid[u] = false; }
+    }
+    if (bad) atomicOr(p.err, ERRBIT_INDEX);
+#pragma unroll
+    for (int n = 0; n < N; ++n) {
+      const int Jn = p.J[n];
+      const bool vec = ((p.vecmask >> n) & 1) != 0;
+#pragma unroll
+      for (int u = 0; u < 2; ++u) {
+        const uint32_t dst = st + uint32_t(((n * 2 + u) * 32 + lane) * 16);
+        const float *src = p.A[n] + int64_t(valid[u] ? nrow[n][u] : 0) * Jn + 4 * t;
+        if (vec) {
+          cp_async16(dst, valid[u] && 4 * t < Jn ? src : p.A[n], valid[u] && 4 * t < Jn ? 16 : 0);
+        } else {
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            const bool in = valid[u] && 4 * t + q < Jn;
+            cp_async4(dst + 4 * q, in ? src + q : p.A[n], in ? 4 : 0);
+          }
+        }
+      }
+    }
+    if (lane < FT_TILE) {
+      const bool in = b + lane < p.end;
+      cp_async4(st + uint32_t(L::ROWS + 4 * lane), in ? p.vals + b + lane : p.vals, in ? 4 : 0);
+    }
+  };
+
+  // prologue: stages 0 .. CORE_STAGES - 2 in flight, the coordinates of the
+  // tile after them in registers
+#pragma unroll
+  for (int s = 0; s < CORE_STAGES - 1; ++s) {
+    const int64_t tile = warp + int64_t(s) * nwarps;
+    if (tile < ntiles) {
+      load_coords(tile);
+      fetch(tile, s);
+    }
+    cp_async_commit();
+  }
+  {
+    const int64_t tile = warp + int64_t(CORE_STAGES - 1) * nwarps;
+    if (tile < ntiles) load_coords(tile);
+  }
+  int s_cur = 0;
+  for (int64_t tile = warp; tile < ntiles; tile += nwarps) {
+    // every lane is done with the stage that the next fetch overwrites
+    __syncwarp();
+    const int64_t ahead = tile + int64_t(CORE_STAGES - 1) * nwarps;
+    const int s_fill = s_cur == 0 ? CORE_STAGES - 1 : s_cur - 1;
+    if (ahead < ntiles) fetch(ahead, s_fill);
+    cp_async_commit();
+    if (ahead + nwarps < ntiles) load_coords(ahead + nwarps);
+    cp_async_wait<CORE_STAGES - 1>();
+    __syncwarp();
+    const unsigned char *st = ring + s_cur * L::STAGE;
+    uint32_t ab[N][2][2];
+#pragma unroll
+    for (int n = 0; n < N; ++n)
+#pragma unroll
+      for (int u = 0; u < 2; ++u) {
+        const float4 v = *reinterpret_cast<const float4 *>(st + ((n * 2 + u) * 32 + lane) * 16);
+        ab[n][u][0] = pack_bf16(v.x, v.y);
+        ab[n][u][1] = pack_bf16(v.z, v.w);
+      }
+    const float *xs = reinterpret_cast<const float *>(st + L::ROWS);
+    float xv[2][2];
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      const float2 x2 = *reinterpret_cast<const float2 *>(xs + 8 * u + 2 * t);
+      xv[u][0] = x2.x;
+      xv[u][1] = x2.y;
+    }
+    core16_tile<N>(p, tab, ab, xv, p.begin + tile * FT_TILE, gs, gc, lane);
+    s_cur = s_cur == CORE_STAGES - 1 ? 0 : s_cur + 1;
+  }
+  cp_async_wait<0>();
+  core16_combine<N>(p, cacc, gs, gc, lane);
+}
+
+// ------------------------------------ core phase, CTA-cooperative (BF16)
+// The core-gradient pass (Algorithm 5) for BF16 at padded rank K = 32, and at
+// K = 16 for orders whose per-lane state does not fit k_core_bf16p.  Since
+// E^(n) = (xhat - x) * A_Psi^(n) (row-wise scaling),
+//   G^(n) = E^(n)T D^(n) = A_Psi^(n)T ((xhat - x) * D^(n)),
+// so the residual is folded into D and the contraction runs over the raw rows.
+// A CTA tile is 8 warp tiles (128 nonzeros):
+//   phase 1  each warp gathers its 16 nonzeros' rows, forms C^(n) = A_Psi B
+//            (Prod), xhat and D^(n), and stores A_Psi^(n) and
+//            (xhat - x) * D^(n) as BF16 rows in shared memory;
+//   phase 2  the N (K/16)^2 output blocks of 16 x 16 (mode n, rows j of
+//            G^(n), columns r) are dealt to the warps; each contracts its
+//            blocks over the 128 nonzeros (ldmatrix.trans operands, 8 k-steps
+//            of mma.sync m16n8k16, FP32 accumulation) and adds the CTA tile's
+//            block into Neumaier (sum, compensation) registers.
+// Every output element has exactly one owning warp, so the CTA partial needs
+// no combine; fixed grid and tile order make the pass reproducible bit for bit.
+template <int N, int K>
+struct CoopSmem {
+  static constexpr int WARPS = 8;
+  static constexpr int ROWS = WARPS * FT_TILE;              // nonzeros per CTA tile
+  static constexpr int LDB = 2 * K + 16;                    // bytes per staged row (conflict-free ldmatrix)
+  static constexpr int BUF = ROWS * LDB;                    // bytes of one [ROWS][K] bf16 buffer
+  static constexpr int TW = Prod<K, MATH_BF16>::WORDS;
+  static constexpr int TAB = N * TW * 4;                    // a.B operand tables
+  static constexpr int UNITS = N * (K / 16) * (K / 16);     // 16 x 16 output blocks
+  static constexpr int UPW = (UNITS + WARPS - 1) / WARPS;   // blocks per warp
+  static constexpr int MINB = (K == 16 && N <= 5) ? 2 : 1;  // CTAs per SM the registers allow
+  static constexpr size_t bytes() { return size_t(TAB) + size_t(2) * N * BUF; }
+};
+
+__device__ __forceinline__ void ldsm_x4_trans(uint32_t addr, uint32_t &r0, uint32_t &r1, uint32_t &r2,
+                                              uint32_t &r3) {
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0, %1, %2, %3}, [%4];"
+               : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
+               : "r"(addr)
+               : "memory");
+}
+
+template <int CPL>
+__device__ __forceinline__ void coop_store(unsigned char *dst, const uint32_t (&v)[CPL / 2]) {
+  if constexpr (CPL == 8) *reinterpret_cast<uint4 *>(dst) = make_uint4(v[0], v[1], v[2], v[3]);
+  else *reinterpret_cast<uint2 *>(dst) = make_uint2(v[0], v[1]);
+}
+
+template <int N, int K>
+__global__ void __launch_bounds__(256, CoopSmem<N, K>::MINB) k_core_coop(const EpochArgs p) {
+  using L = CoopSmem<N, K>;
+  constexpr int CPL = K / 4;
+  constexpr int TW = L::TW;
+  extern __shared__ __align__(16) float smem[];
+  unsigned char *bytes = reinterpret_cast<unsigned char *>(smem);
+  unsigned char *abuf = bytes + L::TAB;                     // [N][ROWS] rows of A_Psi^(n)
+  unsigned char *dbuf = abuf + N * L::BUF;                  // [N][ROWS] rows of (xhat - x) D^(n)
+  const uint32_t abuf_s = static_cast<uint32_t>(__cvta_generic_to_shared(abuf));
+  const uint32_t dbuf_s = static_cast<uint32_t>(__cvta_generic_to_shared(dbuf));
+  fill_tables<N, K, MATH_BF16>(smem, p, false);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int g = lane >> 2, t = lane & 3;
+
+  float gs[L::UPW][8], gc[L::UPW][8];
+#pragma unroll
+  for (int u = 0; u < L::UPW; ++u)
+#pragma unroll
+    for (int i = 0; i < 8; ++i) gs[u][i] = gc[u][i] = 0.f;
+  __syncthreads();
+
+  const int64_t ntiles = (p.end - p.begin + FT_TILE - 1) / FT_TILE;
+  const int64_t nct = (ntiles + L::WARPS - 1) / L::WARPS;
+  TileCoords<N> cur, nxt;
+  if (blockIdx.x < nct) cur.load(p, p.begin + (int64_t(blockIdx.x) * L::WARPS + w) * FT_TILE, lane, true);
+  for (int64_t c = blockIdx.x; c < nct; c += gridDim.x) {
+    const int64_t cn = c + gridDim.x;
+    if (cn < nct) nxt.load(p, p.begin + (cn * L::WARPS + w) * FT_TILE, lane, true);
+    // phase 1: this warp's 16 nonzeros (masked ones leave zero rows)
+    {
+      Front<N, K, MATH_BF16, true> f;
+      f.gather(p, cur, lane);
+      // the raw rows go to shared memory first, so that they need no
+      // registers after C is formed
+#pragma unroll
+      for (int n = 0; n < N; ++n)
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          uint32_t av[CPL / 2];
+#pragma unroll
+          for (int q = 0; q < CPL / 2; ++q) av[q] = pack_bf16(f.a[n][h][2 * q], f.a[n][h][2 * q + 1]);
+          coop_store<CPL>(abuf + n * L::BUF + (FT_TILE * w + g + 8 * h) * L::LDB + 2 * CPL * t, av);
+        }
+      f.compute(smem, TW, lane);
+      float ne[2];
+#pragma unroll
+      for (int h = 0; h < 2; ++h) ne[h] = f.valid[h] ? f.xhat[h] - f.x[h] : 0.f;
+      const bool nonfinite = !isfinite(ne[0]) || !isfinite(ne[1]);
+      if (__any_sync(FULL, nonfinite) && lane == 0) atomicOr(p.err, ERRBIT_NONFINITE);
+#pragma unroll
+      for (int n = 0; n < N; ++n) {
+        float d[2][CPL];
+        f.leave_one_out(n, d);
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          uint32_t dv[CPL / 2];
+#pragma unroll
+          for (int q = 0; q < CPL / 2; ++q) dv[q] = pack_bf16(ne[h] * d[h][2 * q], ne[h] * d[h][2 * q + 1]);
+          coop_store<CPL>(dbuf + n * L::BUF + (FT_TILE * w + g + 8 * h) * L::LDB + 2 * CPL * t, dv);
+        }
+      }
+    }
+    __syncthreads();
+    // phase 2: this warp's output blocks over the CTA tile's 128 nonzeros
+#pragma unroll
+    for (int u = 0; u < L::UPW; ++u) {
+      const int unit = w + L::WARPS * u;
+      if (unit < L::UNITS) {
+        const int n = unit / ((K / 16) * (K / 16));
+        const int mt = (unit / (K / 16)) % (K / 16), np = unit % (K / 16);
+        // ldmatrix.x4.trans: lanes 8q .. 8q + 7 address the 8 rows (nonzeros)
+        // of matrix q.  A operand (A_Psi^T, M = j, K = nonzeros): matrix q
+        // covers nonzeros 8 (q >> 1) + 0..7 and columns j = 16 mt + 8 (q & 1)
+        // + 0..7.  B operand ((xhat - x) D, K = nonzeros, N = r): matrix q
+        // covers nonzeros 8 (q & 1) + 0..7 and r = 16 np + 8 (q >> 1) + 0..7,
+        // i.e. (b0, b1) of the n-tile 16 np and (b0, b1) of 16 np + 8.
+        const int ri = lane & 7, mi = lane >> 3;
+        const uint32_t a_addr = abuf_s + n * L::BUF + (ri + 8 * (mi >> 1)) * L::LDB + 2 * (16 * mt + 8 * (mi & 1));
+        const uint32_t d_addr = dbuf_s + n * L::BUF + (ri + 8 * (mi & 1)) * L::LDB + 2 * (16 * np + 8 * (mi >> 1));
+        float acc[2][4] = {{0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}};
+#pragma unroll
+        for (int kk = 0; kk < L::ROWS / 16; ++kk) {
+          uint32_t a0, a1, a2, a3, b0, b1, b2, b3;
+          ldsm_x4_trans(a_addr + kk * 16 * L::LDB, a0, a1, a2, a3);
+          ldsm_x4_trans(d_addr + kk * 16 * L::LDB, b0, b1, b2, b3);
+          mma_bf16(acc[0], a0, a1, a2, a3, b0, b1);
+          mma_bf16(acc[1], a0, a1, a2, a3, b2, b3);
+        }
+#pragma unroll
+        for (int nt = 0; nt < 2; ++nt)
+#pragma unroll
+          for (int i = 0; i < 4; ++i) neumaier_add(gs[u][4 * nt + i], gc[u][4 * nt + i], acc[nt][i]);
+      }
+    }
+    __syncthreads();
+    cur = nxt;
+  }
+  // CTA partial in the [n][K][K] layout of (sum, compensation) pairs; every
+  // element is written by its owning warp (zero when the CTA had no tiles)
+  float *out = p.partial + size_t(blockIdx.x) * 2 * N * K * K;
+#pragma unroll
+  for (int u = 0; u < L::UPW; ++u) {
+    const int unit = w + L::WARPS * u;
+    if (unit < L::UNITS) {
+      const int n = unit / ((K / 16) * (K / 16));
+      const int mt = (unit / (K / 16)) % (K / 16), np = unit % (K / 16);
+#pragma unroll
+      for (int nt = 0; nt < 2; ++nt)
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          const int j = 16 * mt + g + 8 * (i >> 1), r = 16 * np + 8 * nt + 2 * t + (i & 1);
+          const size_t o = (size_t(n) * K + j) * K + r;
+          out[2 * o] = gs[u][4 * nt + i];
+          out[2 * o + 1] = gc[u][4 * nt + i];
+        }
+    }
   }
 }
 
