@@ -90,6 +90,7 @@ def _declare(lib):
         "orc_factor_epoch": [_INT, _P, _P, _INT, _P, _P, _I64, _P, _P, _I64, _DBL, _DBL, _P],
         "orc_core_grad": [_INT, _P, _INT, _P, _P, _I64, _P, _P, _P, _INT],
         "orc_core_epoch": [_INT, _P, _INT, _P, _P, _I64, _P, _P, _DBL, _DBL, _INT],
+        "orc_core_epoch_sgd": [_INT, _P, _INT, _P, _P, _I64, _P, _P, _I64, _DBL, _DBL, _INT],
         "orc_errors": [_INT, _P, _INT, _P, _P, _I64, _P, _P, _P, _INT],
         "orc_objective": [_INT, _P, _P, _INT, _P, _P, _I64, _P, _P, _DBL, _DBL, _P, _INT],
         "orc_row_stats": [_INT, _P, _P, _INT, _P, _P, _I64, _P, _P, _DBL, _DBL, _DBL, _P, _P, _P],
@@ -224,6 +225,18 @@ def core_epoch(A, B, idx, x, gamma: float, lam: float, nthreads: int = 1):
     xv = np.ascontiguousarray(x, dtype=np.float64)
     _check(load().orc_core_epoch(m.N, _ptr(m.J), m.R, m.pA, m.pB, nnz, pidx, _ptr(xv),
                                  float(gamma), float(lam), nthreads), "orc_core_epoch")
+    return m.B
+
+
+def core_epoch_sgd(A, B, idx, x, S: int, gamma: float, lam: float, nthreads: int = 1):
+    """Core phase in the per-sample-set reading of Algorithm 3: consecutive
+    sets of S nonzeros, one averaged core step per set; returns the new core
+    matrices."""
+    m = _Model(A, [np.array(b, dtype=np.float64, copy=True) for b in B])
+    cols, pidx, nnz = _coords(idx, m.N)
+    xv = np.ascontiguousarray(x, dtype=np.float64)
+    _check(load().orc_core_epoch_sgd(m.N, _ptr(m.J), m.R, m.pA, m.pB, nnz, pidx, _ptr(xv), int(S),
+                                     float(gamma), float(lam), nthreads), "orc_core_epoch_sgd")
     return m.B
 
 

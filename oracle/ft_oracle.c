@@ -312,6 +312,29 @@ done:
 }
 
 /*
+ * Core phase in the per-sample-set reading of Algorithm 3, whose core loop
+ * applies rule "Update_FastTuckerPlus_core" for every sampled set Psi: the
+ * nonzeros are taken in stored order in consecutive sets of S, and each set
+ * makes one step of Algorithm 5 restricted to it, from the core matrices as
+ * they were at the set's start:
+ *     B^(n) <- B^(n) - gamma (sum_Psi G^(n) / |Psi| + lambda B^(n))
+ * S >= nnz is one step of Algorithm 5 (orc_core_epoch).
+ */
+int orc_core_epoch_sgd(int N, const int *J, int R, double *const *A, double *const *B,
+                       int64_t nnz, const int32_t *const *idx, const double *x, int64_t S,
+                       double gamma, double lambda, int nthreads) {
+  if (orc_check_shape(N, J, R) || S < 1) return ORC_EARG;
+  for (int64_t lo = 0; lo < nnz; lo += S) {
+    const int64_t cnt = (nnz - lo < S) ? nnz - lo : S;
+    const int32_t *set_idx[ORC_MAX_ORDER];
+    for (int n = 0; n < N; ++n) set_idx[n] = idx[n] + lo;
+    const int rc = orc_core_epoch(N, J, R, A, B, cnt, set_idx, x + lo, gamma, lambda, nthreads);
+    if (rc) return rc;
+  }
+  return ORC_OK;
+}
+
+/*
  * Test-set errors (Sec. 5.2): out[0] = RMSE = sqrt(sum e^2 / n),
  * out[1] = MAE = sum |e| / n, out[2] = sum e^2, with e = x - xhat.
  */

@@ -147,6 +147,44 @@ def pin_core_epoch_step(seed=3):
         np.testing.assert_allclose(Bn[n], B[n] - gamma * fd, rtol=1e-7, atol=1e-8)
 
 
+def pin_core_sgd_sets(seed=12):
+    """Per-set core SGD (Algorithm 3's core loop): each consecutive set of S
+    nonzeros is a gradient step on its own averaged objective
+    sum_Psi(1/2 e^2)/|Psi| + 1/2 lambda ||B||^2, by central differences
+    through the dense model, taken from the core matrices left by the
+    previous set (S = 1: one rule-"Update_FastTuckerPlus_core" step per
+    nonzero; a ragged last set)."""
+    rng = np.random.default_rng(seed)
+    h = 1e-6
+    N, J, R = 3, (2, 3, 2), 2
+    A, B, idx, x = rand_problem(rng, N, [3, 4, 3], J, R, 7)
+    gamma, lam = 0.1, 0.15
+    for S in (1, 3):
+        want = [b.copy() for b in B]
+        for lo in range(0, len(x), S):
+            ms = range(lo, min(lo + S, len(x)))
+
+            def obj(Bs):
+                s = sum(0.5 * (x[m] - dense_predict(A, Bs, idx[:, m])) ** 2 for m in ms)
+                return s / len(ms) + 0.5 * lam * sum(float((b * b).sum()) for b in Bs)
+
+            step = []
+            for n in range(N):
+                fd = np.empty((J[n], R))
+                for j in range(J[n]):
+                    for r in range(R):
+                        Bp = [b.copy() for b in want]
+                        Bm = [b.copy() for b in want]
+                        Bp[n][j, r] += h
+                        Bm[n][j, r] -= h
+                        fd[j, r] = (obj(Bp) - obj(Bm)) / (2 * h)
+                step.append(gamma * fd)
+            want = [b - st for b, st in zip(want, step)]
+        got = oracle.core_epoch_sgd(A, B, idx, x, S, gamma, lam)
+        for n in range(N):
+            np.testing.assert_allclose(got[n], want[n], rtol=1e-7, atol=1e-8)
+
+
 def pin_cp_special_case(seed=4):
     """B = I, J = R: one sequential epoch is CP-SGD on x ~ sum_r prod_n a^(n)_r."""
     rng = np.random.default_rng(seed)
@@ -340,7 +378,7 @@ def pin_planted_recovery(seed=11):
     assert r1 < 0.05 * r0, (r0, r1)
 
 
-PINS = [pin_predict_dense, pin_factor_grad_fd, pin_core_grad_fd, pin_core_epoch_step,
+PINS = [pin_predict_dense, pin_factor_grad_fd, pin_core_grad_fd, pin_core_epoch_step, pin_core_sgd_sets,
         pin_cp_special_case, pin_mf_special_case, pin_full_batch_is_sum_of_fd_grads,
         pin_disjoint_rows_batch_invariance, pin_duplicate_doubles_step,
         pin_planted_fixed_point, pin_hand_worked, pin_errors_definition, pin_planted_recovery]
@@ -365,6 +403,9 @@ MUTANTS = [
      "g[j] = -e * dbt + lambda * a[j];"),
     ("update_sign_flipped", "a[j] -= gamma * s * g[j];", "a[j] += gamma * s * g[j];"),
     ("mae_squared", "ae += fabs(e);", "ae += e * e;"),
+    ("core_sgd_values_of_first_set", "x + lo, gamma, lambda, nthreads);", "x, gamma, lambda, nthreads);"),
+    ("core_sgd_first_set_only", "for (int64_t lo = 0; lo < nnz; lo += S) {",
+     "for (int64_t lo = 0; lo < nnz && lo < S; lo += S) {"),
 ]
 
 
