@@ -254,7 +254,8 @@ def run_ours(args, rank, world, local_rank):
     nnz_train, nnz_test = int(trx.numel()), int(tex.numel())
     stream = torch.cuda.current_stream(dev)
     m = ft.FastTuckerPlus(tri, trx, A, B, precision=args.precision, scatter="hogwild",
-                          hot_rows=args.hot_rows, hot_window=args.hot_window, engine=args.engine)
+                          hot_rows=args.hot_rows, hot_window=args.hot_window, engine=args.engine,
+                          core_scheme=args.core_scheme)
 
     ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
 
@@ -344,7 +345,8 @@ def run_ours(args, rank, world, local_rank):
         "config": {
             "workload": args.workload if args.nnz is None else f"{args.workload} at {args.nnz} coordinates", "N": N, "I": list(w.I), "J": J, "R": R,
             "nnz_train": nnz_train, "nnz_test": nnz_test, "precision": args.precision,
-            "scatter": "hogwild", "engine": args.engine, "hot_rows": m.cfg.hot_rows,
+            "scatter": "hogwild", "engine": args.engine, "core_scheme": args.core_scheme,
+            "hot_rows": m.cfg.hot_rows,
             "hot_window": m.cfg.hot_window,
             "lr_a": LR, "lr_b": LR_B, "lambda": LAM,
             "parallelism": "replicas" if world > 1 else "single",
@@ -403,10 +405,11 @@ def engine_for(args, N, J, R):
 
 
 def run_sweep(args, local_rank):
-    """The paper's scaling studies on this GPU (Sec. 5): per-iteration factor
-    and core times (a) over the synthetic orders N = 3..10 (I = 10,000 per
-    mode, 1e8 uniform coordinates, J = R = 16) and (b) over (R, J) in
-    {16, 32}^2 on the Netflix-shaped Zipf tensor."""
+    """The paper's studies on this GPU (Sec. 5): per-iteration factor and core
+    times (a) over the synthetic orders N = 3..10 (I = 10,000 per mode, 1e8
+    uniform coordinates, J = R = 16), (b) over (R, J) in {16, 32}^2 on the
+    Netflix-shaped Zipf tensor, (c) for the two core-phase schemes of
+    Sec. 5.6 (calculation vs storage) per precision on that tensor."""
     dev = torch.device(f"cuda:{local_rank}")
     torch.cuda.set_device(dev)
     ft.load()
@@ -446,6 +449,21 @@ def run_sweep(args, local_rank):
                          "factor_ms": f, "core_ms": c, "factor_x": f / base[0], "core_x": c / base[1],
                          "value": nnz / ((f + c) / 1e3)})
             m.close()
+    if args.sweep in ("schemes", "all"):
+        # Sec. 5.6: the core phase forming the rows of C per nonzero
+        # (calculation) or gathering them from C = A B precomputed once per
+        # core phase (storage), on CUDA cores (FP32) and tensor cores
+        w0, tri, trx, tei, tex, A0, B0 = make_workload(dev, args.nnz, args.workload)
+        for prec in ("fp32", "tf32", "bf16"):
+            for scheme in ("calc", "store"):
+                A = [a.clone() for a in A0]
+                B = [b.clone() for b in B0]
+                m = ft.FastTuckerPlus(tri, trx, A, B, precision=prec, hot_rows=args.hot_rows,
+                                      hot_window=args.hot_window, core_scheme=scheme)
+                f, c = time_phases(m, args.steps, args.warmup, stream)
+                rows.append({"study": "core_scheme", "workload": w0.name, "precision": prec, "scheme": scheme,
+                             "nnz_train": int(trx.numel()), "factor_ms": f, "core_ms": c})
+                m.close()
     return {"metric": METRIC, "unit": UNIT, "sweep": args.sweep, "precision": args.precision,
             "steps": args.steps, "warmup": args.warmup, "peak_hbm_gbs": peak, "peak_kind": peak_kind,
             "data": "synthetic", "rows": rows}
@@ -648,11 +666,15 @@ def main():
     ap.add_argument("--engine", choices=["warp", "tcgen05"], default="warp",
                     help="factor-pass kernels: 16-nonzero warp tiles (mma.sync) or 128-nonzero "
                          "warpgroup tiles (tcgen05.mma, TMEM)")
+    ap.add_argument("--core-scheme", choices=["calc", "store"], default="calc",
+                    help="core phase: rows of C formed per nonzero, or gathered from C = A B "
+                         "precomputed once per core phase (Sec. 5.6)")
     ap.add_argument("--workload", default=WORKLOAD, choices=sorted(synth.WORKLOADS) + [BATCHED],
                     help="the timed tensor (default: the Netflix-shaped 1e8 Zipf tensor)")
-    ap.add_argument("--sweep", choices=["orders", "ranks", "all"], default=None,
-                    help="instead of the headline line: the order sweep N = 3..10 and/or the "
-                         "(R, J) sweep, per-iteration phase times")
+    ap.add_argument("--sweep", choices=["orders", "ranks", "schemes", "all"], default=None,
+                    help="instead of the headline line: the order sweep N = 3..10, the (R, J) "
+                         "sweep and/or the core-phase schemes (calculation vs storage) per "
+                         "precision, per-iteration phase times")
     ap.add_argument("--nnz", type=int, default=None,
                     help="distinct coordinates drawn (default: the workload's 1e8); "
                          "a smaller case of the same recipe, e.g. for profiling")

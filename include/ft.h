@@ -104,13 +104,24 @@ typedef struct {
    * accumulators (FT_BF16, J_n, R <= 16, N <= 4, FT_HOGWILD only; other
    * configurations return FT_ERR_ARG from ft_workspace_size / ft_init). */
   int engine;
-  int reserved[3];     /* must be zero */
+  /* How the core phase obtains the rows c^(n) = a^(n) B^(n) (Sec. 5.6,
+   * "Replace memory access with calculation"): FT_CORE_CALC (default) forms
+   * them for every nonzero from the gathered factor rows (Algorithm 5);
+   * FT_CORE_STORE first computes C^(n) = A^(n) B^(n) for every row of every
+   * mode (FP32, one dense product per core phase, I_n x K floats of
+   * workspace per mode) and gathers its rows instead.  The paper found the
+   * storage scheme faster on CUDA cores and calculation faster with tensor
+   * cores.  Both give the same gradient up to rounding. */
+  int core_scheme;
+  int reserved[2];     /* must be zero */
 } ft_config;
 
 enum { FT_ENGINE_WARP = 0, FT_ENGINE_TCGEN05 = 1 };
+enum { FT_CORE_CALC = 0, FT_CORE_STORE = 1 };
 
 /* Fill *cfg with the defaults: FT_FP32, FT_HOGWILD, det_batch 4096, automatic
- * grid, hot_rows -1, hot_window 64, hot_min_count 2. */
+ * grid, hot_rows -1, hot_window 64, hot_min_count 2, FT_ENGINE_WARP,
+ * FT_CORE_CALC. */
 void ft_config_default(ft_config *cfg);
 
 /* Bytes of device workspace needed by ft_init for this problem (host call;
@@ -145,6 +156,37 @@ ft_status ft_epoch_factors(ft_ctx *ctx, float lr_a, float lambda_a,
  * nonzeros with compensated float32 sums in a fixed order (reproducible bit
  * for bit), then B^(n) <- B^(n) - lr_b (G^(n)/nnz + lambda_b B^(n)). */
 ft_status ft_epoch_core(ft_ctx *ctx, float lr_b, float lambda_b, void *stream);
+
+/* Reshuffle the training nonzeros (Algorithm 3 takes the sample sets Psi
+ * from Omega at random in every iteration): the context's nonzeros are
+ * gathered in the order perm gives into caller-provided arrays,
+ *   idx_out[n][m] = idx[n][perm[m]],  vals_out[m] = vals[perm[m]],
+ * and the context then borrows idx_out / vals_out (the arrays it used before
+ * are no longer read and may be reused, e.g. as the next call's outputs).
+ *   perm      device, nnz int32, a permutation of 0..nnz-1 drawn by the
+ *             caller (repeated entries are not detected and duplicate
+ *             nonzeros)
+ *   idx_out   host array of N device pointers, nnz int32 each; vals_out
+ *             device, nnz floats; none may alias the current arrays
+ *             (FT_ERR_ARG)
+ * The hot-row coordinates of the Hogwild pass are rebuilt on the device; in
+ * FT_DETERMINISTIC mode the per-batch row grouping is rebuilt on the host
+ * (synchronises).  An entry of perm outside [0, nnz) is latched as
+ * FT_ERR_INDEX (reported by the next synchronising call) and copies nonzero
+ * 0 in its place. */
+ft_status ft_permute(ft_ctx *ctx, const int32_t *perm, int32_t *const *idx_out, float *vals_out,
+                     void *stream);
+
+/* One core phase in the per-sample-set reading of Algorithm 3, whose core
+ * loop applies rule "Update_FastTuckerPlus_core" for every sampled set Psi:
+ * the training nonzeros are taken in stored order in consecutive sets of
+ * set_size (the last one ragged), and each set makes one step of
+ * ft_epoch_core restricted to it, from the core matrices the previous set
+ * left: B^(n) <- B^(n) - lr_b (G_Psi^(n) / |Psi| + lambda_b B^(n)).
+ * set_size >= nnz is ft_epoch_core.  Each set is one core-gradient pass plus
+ * one finalize (and, with FT_CORE_STORE, one C = A B product), in a fixed
+ * order: reproducible bit for bit.  set_size < 1: FT_ERR_ARG. */
+ft_status ft_epoch_core_sgd(ft_ctx *ctx, float lr_b, float lambda_b, int64_t set_size, void *stream);
 
 /* The core gradient alone, without touching B:
  * G_out (device) receives G^(n) = sum_Omega (xhat - x) a^(n)T d^(n) for

@@ -101,6 +101,39 @@ struct FinalizeArgs {
 
 // Core finalize (Algorithm 5): G^(n) = sum over CTA partials (compensated,
 // fixed order); B <- B - lr (G / |Omega| + lam B).
+// Storage scheme of the core phase (Sec. 5.6): C^(n) = A^(n) B^(n) for every
+// row of every mode, FP32, row-major I_n x K with zeros in columns >= R.
+// Thread e computes four columns of one row (summing over j in order).
+struct StoreArgs {
+  const float *A[FT_MAXN];
+  const float *B[FT_MAXN];
+  float *C[FT_MAXN];
+  int64_t I[FT_MAXN];
+  int J[FT_MAXN];
+  int64_t chunk_begin[FT_MAXN + 1];   // first 4-column chunk of each mode
+  int N, K, R;
+};
+
+__global__ void k_store_c(const StoreArgs a) {
+  const int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (e >= a.chunk_begin[a.N]) return;
+  int n = 0;
+  while (n + 1 < a.N && e >= a.chunk_begin[n + 1]) ++n;
+  const int64_t local = e - a.chunk_begin[n];
+  const int64_t row = local / (a.K / 4);
+  const int r0 = 4 * int(local % (a.K / 4));
+  const float *arow = a.A[n] + row * a.J[n];
+  float acc[4] = {0.f, 0.f, 0.f, 0.f};
+  for (int j = 0; j < a.J[n]; ++j) {
+    const float av = __ldg(arow + j);
+    const float *brow = a.B[n] + int64_t(j) * a.R;
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+      if (r0 + q < a.R) acc[q] = fmaf(av, __ldg(brow + r0 + q), acc[q]);
+  }
+  *reinterpret_cast<float4 *>(a.C[n] + row * a.K + r0) = make_float4(acc[0], acc[1], acc[2], acc[3]);
+}
+
 __global__ void k_finalize(const FinalizeArgs f) {
   const int tid = blockIdx.x * blockDim.x + threadIdx.x;
   const int KK = f.K * f.K;
@@ -172,6 +205,33 @@ __global__ void k_remap(const RemapArgs a) {
     }
 }
 
+// Reordered copy of the nonzeros: out[n][m] = idx[n][perm[m]],
+// vals_out[m] = vals[perm[m]].  An entry of perm outside [0, nnz) latches
+// ERRBIT_INDEX and copies nonzero 0 instead (the arrays stay valid).
+struct PermuteArgs {
+  const int32_t *idx[FT_MAXN];
+  int32_t *out[FT_MAXN];
+  const float *vals;
+  float *vals_out;
+  const int32_t *perm;
+  int N;
+  int64_t nnz;
+  int *err;
+};
+
+__global__ void k_permute(const PermuteArgs a) {
+  for (int64_t m = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; m < a.nnz;
+       m += int64_t(gridDim.x) * blockDim.x) {
+    int64_t q = a.perm[m];
+    if (q < 0 || q >= a.nnz) {
+      atomicOr(a.err, ft::ERRBIT_INDEX);
+      q = 0;
+    }
+    for (int n = 0; n < a.N; ++n) a.out[n][m] = __ldg(a.idx[n] + q);
+    a.vals_out[m] = __ldg(a.vals + q);
+  }
+}
+
 struct RowFinishArgs {
   const float *gsum, *cnt, *esum, *hsum;
   int N;
@@ -231,8 +291,12 @@ struct Plan {
   // workspace offsets
   size_t off_err = 0, off_out = 0, off_partial = 0, off_errpart = 0, off_delta = 0;
   size_t off_order = 0, off_segptr = 0, off_segrow = 0;
-  size_t off_remap = 0, off_hot = 0, off_counts = 0, off_stats = 0, total = 0;
+  size_t off_remap = 0, off_hot = 0, off_counts = 0, off_stats = 0, off_cst = 0, total = 0;
   int64_t rows = 0, grows = 0;      // sum I_n and sum I_n J_n
+  // core-gradient kernel of the configured scheme (calculation or storage)
+  const void *core_fn = nullptr;
+  size_t core_smem = 0;
+  int core_threads = 256;
 };
 
 // Shared memory of the hot-row cache: with two 256-thread CTAs per SM (the
@@ -277,8 +341,9 @@ ft_status make_plan(int N, const int64_t *I, const int *J, int R, int64_t nnz, c
   if (c.scatter == FT_DETERMINISTIC && c.det_batch < 1) return FT_ERR_ARG;
   if (c.blocks_per_sm < 0) return FT_ERR_ARG;
   if (c.hot_rows < -1 || c.hot_window < 1 || c.hot_min_count < 1) return FT_ERR_ARG;
-  for (int q = 0; q < 3; ++q)
+  for (int q = 0; q < 2; ++q)
     if (c.reserved[q] != 0) return FT_ERR_ARG;
+  if (c.core_scheme != FT_CORE_CALC && c.core_scheme != FT_CORE_STORE) return FT_ERR_ARG;
   if (c.engine != FT_ENGINE_WARP && c.engine != FT_ENGINE_TCGEN05) return FT_ERR_ARG;
   if (c.engine == FT_ENGINE_TCGEN05 && (c.scatter != FT_HOGWILD || c.precision != FT_BF16)) return FT_ERR_ARG;
   int maxr = R;
@@ -338,7 +403,11 @@ ft_status make_plan(int N, const int64_t *I, const int *J, int R, int64_t nnz, c
   }
   const int occ_f = occupancy(p->ks.factor, 256, tc ? p->ks.factor_smem : p->factor_smem);
   const int occ_d = occupancy(p->ks.factor_delta, 256, p->ks.factor_smem);
-  const int occ_c = occupancy(p->ks.core, p->ks.core_threads, p->ks.core_smem);
+  const bool store = c.core_scheme == FT_CORE_STORE;
+  p->core_fn = store ? p->ks.core_store : p->ks.core;
+  p->core_smem = store ? p->ks.core_store_smem : p->ks.core_smem;
+  p->core_threads = store ? p->ks.core_store_threads : p->ks.core_threads;
+  const int occ_c = occupancy(p->core_fn, p->core_threads, p->core_smem);
   const int occ_p = occupancy(p->es.predict, 256, p->es.smem);
   const int occ_e = occupancy(p->es.errors, 256, p->es.smem);
   if (occ_f < 1 || occ_d < 1 || occ_c < 1 || occ_p < 1 || occ_e < 1) return FT_ERR_CUDA;
@@ -374,6 +443,9 @@ ft_status make_plan(int N, const int64_t *I, const int *J, int R, int64_t nnz, c
     p->grows += I[n] * J[n];
   }
   p->off_stats = off; off += align_up(sizeof(float) * size_t(p->grows + 3 * p->rows));
+  if (store) {
+    p->off_cst = off; off += align_up(sizeof(float) * size_t(p->rows) * K);
+  }
   p->total = off;
   return FT_OK;
 }
@@ -486,6 +558,25 @@ ft_status build_segments(ft_ctx *c, cudaStream_t st) {
   return FT_OK;
 }
 
+// The Hogwild pass's copy of the coordinates with cached rows remapped to
+// -(slot + 1); the slot of each row (or -1) sits in the counts region.
+ft_status remap_hot(ft_ctx *c, cudaStream_t st) {
+  const Plan &p = c->p;
+  RemapArgs ra;
+  memset(&ra, 0, sizeof(ra));
+  int64_t off = 0;
+  for (int n = 0; n < p.N; ++n) {
+    ra.idx[n] = c->idx[n];
+    ra.out[n] = ws_ptr<int32_t>(c, p.off_remap) + size_t(n) * p.nnz;
+    ra.slot_of[n] = ws_ptr<int32_t>(c, p.off_counts) + off;
+    off += p.I[n];
+  }
+  ra.N = p.N;
+  ra.nnz = p.nnz;
+  const int grid = int(std::min<int64_t>((p.nnz + 255) / 256, int64_t(p.num_sms) * 8));
+  return launch(c, reinterpret_cast<const void *>(&k_remap), grid, 256, 0, &ra, st);
+}
+
 // Hot-row cache of the Hogwild pass: count the nonzeros of every row, keep
 // the hot_cap most frequent rows of each mode that have at least
 // hot_min_count of them, and write the remapped coordinates.
@@ -552,18 +643,7 @@ ft_status build_hot_cache(ft_ctx *c, cudaStream_t st) {
       cudaMemcpyAsync(d_counts, slot_of.data(), sizeof(int32_t) * sumI, cudaMemcpyHostToDevice, st) !=
           cudaSuccess)
     return FT_ERR_CUDA;
-  RemapArgs ra;
-  memset(&ra, 0, sizeof(ra));
-  off = 0;
-  for (int n = 0; n < p.N; ++n) {
-    ra.idx[n] = c->idx[n];
-    ra.out[n] = ws_ptr<int32_t>(c, p.off_remap) + size_t(n) * p.nnz;
-    ra.slot_of[n] = d_counts + off;
-    off += p.I[n];
-  }
-  ra.N = p.N;
-  ra.nnz = p.nnz;
-  s = launch(c, reinterpret_cast<const void *>(&k_remap), grid, 256, 0, &ra, st);
+  s = remap_hot(c, st);
   if (s != FT_OK) return s;
   return cudaStreamSynchronize(st) == cudaSuccess ? FT_OK : FT_ERR_CUDA;
 }
@@ -728,12 +808,41 @@ ft_status ft_epoch_factors(ft_ctx *c, float lr_a, float lambda_a, const float *c
   return FT_OK;
 }
 
+// Core gradient over the nonzeros [lo, hi) and, with update, the step
+// B <- B - lr_b (G / (hi - lo) + lambda_b B) (Algorithm 5 on that range).
 static ft_status core_pass(ft_ctx *c, float lr_b, float lambda_b, float *G_out, int update,
-                           cudaStream_t st) {
+                           cudaStream_t st, int64_t lo = 0, int64_t hi = -1) {
   const Plan &p = c->p;
+  if (hi < 0) hi = p.nnz;
   ft::EpochArgs a = base_args(c);
+  a.begin = lo;
+  a.end = hi;
   a.partial = ws_ptr<float>(c, p.off_partial);
-  ft_status s = launch(c, p.ks.core, p.grid_core, p.ks.core_threads, p.ks.core_smem, &a, st);
+  ft_status s = FT_OK;
+  if (p.cfg.core_scheme == FT_CORE_STORE) {
+    // storage scheme: C^(n) = A^(n) B^(n) for every row, then the pass reads it
+    StoreArgs sa;
+    memset(&sa, 0, sizeof(sa));
+    sa.N = p.N;
+    sa.K = p.K;
+    sa.R = p.R;
+    int64_t off = 0;
+    for (int n = 0; n < p.N; ++n) {
+      sa.A[n] = c->A[n];
+      sa.B[n] = c->B[n];
+      sa.J[n] = p.J[n];
+      sa.I[n] = p.I[n];
+      sa.C[n] = ws_ptr<float>(c, p.off_cst) + off * p.K;
+      a.cst[n] = sa.C[n];
+      sa.chunk_begin[n] = off * (p.K / 4);
+      off += p.I[n];
+    }
+    sa.chunk_begin[p.N] = off * (p.K / 4);
+    const int64_t chunks = sa.chunk_begin[p.N];
+    s = launch(c, reinterpret_cast<const void *>(&k_store_c), int((chunks + 255) / 256), 256, 0, &sa, st);
+    if (s != FT_OK) return s;
+  }
+  s = launch(c, p.core_fn, p.grid_core, p.core_threads, p.core_smem, &a, st);
   if (s != FT_OK) return s;
   FinalizeArgs f;
   memset(&f, 0, sizeof(f));
@@ -752,7 +861,7 @@ static ft_status core_pass(ft_ctx *c, float lr_b, float lambda_b, float *G_out, 
   f.G_out = G_out;
   f.lr = lr_b;
   f.lam = lambda_b;
-  f.inv_nnz = p.nnz > 0 ? float(1.0 / double(p.nnz)) : 0.f;
+  f.inv_nnz = hi > lo ? float(1.0 / double(hi - lo)) : 0.f;
   f.update = update;
   const int total = p.N * p.K * p.K;
   return launch(c, reinterpret_cast<const void *>(&k_finalize), (total + 255) / 256, 256, 0, &f, st);
@@ -762,6 +871,52 @@ ft_status ft_epoch_core(ft_ctx *c, float lr_b, float lambda_b, void *stream) {
   if (!c) return FT_ERR_ARG;
   if (!std::isfinite(lr_b) || !std::isfinite(lambda_b)) return FT_ERR_ARG;
   return core_pass(c, lr_b, lambda_b, nullptr, 1, static_cast<cudaStream_t>(stream));
+}
+
+ft_status ft_permute(ft_ctx *c, const int32_t *perm, int32_t *const *idx_out, float *vals_out,
+                     void *stream) {
+  if (!c) return FT_ERR_ARG;
+  const Plan &p = c->p;
+  if (p.nnz == 0) return FT_OK;
+  if (!perm || !idx_out || !vals_out || vals_out == c->vals) return FT_ERR_ARG;
+  for (int n = 0; n < p.N; ++n)
+    for (int k = 0; k < p.N; ++k)
+      if (!idx_out[n] || idx_out[n] == c->idx[k]) return FT_ERR_ARG;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  PermuteArgs a;
+  memset(&a, 0, sizeof(a));
+  for (int n = 0; n < p.N; ++n) {
+    a.idx[n] = c->idx[n];
+    a.out[n] = idx_out[n];
+  }
+  a.vals = c->vals;
+  a.vals_out = vals_out;
+  a.perm = perm;
+  a.N = p.N;
+  a.nnz = p.nnz;
+  a.err = ws_ptr<int>(c, p.off_err);
+  const int grid = int(std::min<int64_t>((p.nnz + 255) / 256, int64_t(p.num_sms) * 8));
+  ft_status s = launch(c, reinterpret_cast<const void *>(&k_permute), grid, 256, 0, &a, st);
+  if (s != FT_OK) return s;
+  for (int n = 0; n < p.N; ++n) c->idx[n] = idx_out[n];
+  c->vals = vals_out;
+  if (c->hot_active) {
+    s = remap_hot(c, st);
+    if (s != FT_OK) return s;
+  }
+  if (p.cfg.scatter == FT_DETERMINISTIC) return build_segments(c, st);
+  return FT_OK;
+}
+
+ft_status ft_epoch_core_sgd(ft_ctx *c, float lr_b, float lambda_b, int64_t set_size, void *stream) {
+  if (!c || set_size < 1) return FT_ERR_ARG;
+  if (!std::isfinite(lr_b) || !std::isfinite(lambda_b)) return FT_ERR_ARG;
+  const cudaStream_t st = static_cast<cudaStream_t>(stream);
+  for (int64_t lo = 0; lo < c->p.nnz; lo += set_size) {
+    const ft_status s = core_pass(c, lr_b, lambda_b, nullptr, 1, st, lo, std::min(c->p.nnz, lo + set_size));
+    if (s != FT_OK) return s;
+  }
+  return FT_OK;
 }
 
 ft_status ft_core_grad(ft_ctx *c, float *G_out, void *stream) {

@@ -70,6 +70,9 @@ struct EpochArgs {
   int hot_base[FT_MAXN + 1];
   int hot_cap;                      // slots in shared memory (0 = no cache)
   int hot_window;                   // CTA tiles between write-back/refresh
+  // Storage scheme of the core pass: C^(n) = A^(n) B^(n) precomputed for
+  // every row, row-major I_n x K (columns >= R are zero), or null.
+  const float *cst[FT_MAXN];
 };
 
 // Mode of a cache slot.
@@ -426,6 +429,29 @@ struct Front {
     // tabB: table of product a.B of mode n at tabB + n * tab_words
 #pragma unroll
     for (int n = 0; n < N; ++n) Prod<K, MATH>::run(a[n], tabB + n * tab_words, c[n], lane);
+    predict();
+  }
+
+  // Storage scheme (Sec. 5.6, "Replace memory access with calculation"): the
+  // rows of C^(n) = A^(n) B^(n) are read from p.cst instead of formed here.
+  __device__ __forceinline__ void load_stored(const EpochArgs &p, int lane) {
+    const int t = lane & 3;
+#pragma unroll
+    for (int n = 0; n < N; ++n)
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const float *src = p.cst[n] + int64_t(row[n][h]) * K + CPL * t;
+#pragma unroll
+        for (int w = 0; w < CPL; w += 4) {
+          float4 f4 = make_float4(0.f, 0.f, 0.f, 0.f);
+          if (valid[h]) f4 = __ldg(reinterpret_cast<const float4 *>(src + w));
+          c[n][h][w] = f4.x; c[n][h][w + 1] = f4.y; c[n][h][w + 2] = f4.z; c[n][h][w + 3] = f4.w;
+        }
+      }
+    predict();
+  }
+
+  __device__ __forceinline__ void predict() {
     // xhat = sum_r prod_n c^(n)_r: lane partial over its chunk, then the group of four
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
@@ -736,7 +762,8 @@ struct CoreSmem {
   }
 };
 
-template <int N, int K, int MATH>
+// STORE: the storage scheme (rows of C read from p.cst, Sec. 5.6).
+template <int N, int K, int MATH, bool STORE = false>
 __global__ void __launch_bounds__(256) k_core(const EpochArgs p) {
   extern __shared__ __align__(16) float smem[];
   using L = CoreSmem<N, K, MATH>;
@@ -761,7 +788,8 @@ __global__ void __launch_bounds__(256) k_core(const EpochArgs p) {
   for (int64_t tile = warp; tile < ntiles; tile += nwarps) {
     Front<N, K, MATH, true> f;
     f.load(p, p.begin + tile * FT_TILE, lane, true);
-    f.compute(smem, TW, lane);
+    if constexpr (STORE) f.load_stored(p, lane);
+    else f.compute(smem, TW, lane);
     const float ne0 = f.xhat[0] - f.x[0], ne1 = f.xhat[1] - f.x[1];
 #pragma unroll
     for (int n = 0; n < N; ++n) {
@@ -810,327 +838,6 @@ __global__ void __launch_bounds__(256) k_core(const EpochArgs p) {
   }
 }
 
-// ------------------------------------------- core phase, BF16 in registers
-// Tile arithmetic of the core-gradient pass (Algorithm 5) for K = 16 with
-// BF16 tensor cores (core16_tile), arranged so that no operand of the
-// products is staged through shared memory:
-//   * C^T = B^T A_Psi^T (mma m16n8k16, M = r, N = the tile's 16 nonzeros,
-//     K = j): the gathered rows, packed to bf16, are already the B operand,
-//     and the accumulator (rows r = g, g + 8; columns m = 2t, 2t + 1 of each
-//     8-nonzero n-tile) is the A-operand layout of the next product;
-//   * D^T = *_{k != n} C^(k)T elementwise; xhat_m by a reduction over r
-//     (3 xor-shuffles over g);
-//   * G^T = D^T E (M = r, N = j, K = the 16 nonzeros): E = (xhat - x) * A_Psi
-//     in the B-operand layout comes from the packed rows by movmatrix.trans
-//     (an 8 x 8 transpose of 16-bit fragments), scaled per nonzero;
-//   * the tile's G^T is added into Neumaier (sum, compensation) registers.
-// Logical contraction index k of the first product maps to the physical
-// column chunk the lane gathered: k = 2t, 2t + 1, 2t + 8, 2t + 9 are
-// columns 4t .. 4t + 3.
-__device__ __forceinline__ int phys_col16(int k) { return 4 * ((k & 7) >> 1) + 2 * (k >> 3) + (k & 1); }
-
-__device__ __forceinline__ uint32_t movmatrix_trans(uint32_t x) {
-  uint32_t y;
-  asm volatile("movmatrix.sync.aligned.m8n8.trans.b16 %0, %1;\n" : "=r"(y) : "r"(x));
-  return y;
-}
-
-__device__ __forceinline__ uint32_t scale_bf16x2(uint32_t v, float s0, float s1) {
-  __nv_bfloat162 h = *reinterpret_cast<__nv_bfloat162 *>(&v);
-  const float2 f = __bfloat1622float2(h);
-  return pack_bf16(f.x * s0, f.y * s1);
-}
-
-template <int N>
-struct CoreRegSmem {
-  static constexpr int TABW = 4 * 32;                  // A-operand words (B^T) per mode
-  static constexpr int ACC = 2 * 8 * 32;               // (sum, comp) x 8 values x 32 lanes per mode
-  static constexpr size_t bytes() { return sizeof(uint32_t) * (size_t(N) * TABW) + sizeof(float) * N * ACC; }
-};
-
-// B^T as the A operand of C^T = B^T A_Psi^T, one table per mode: register q of
-// lane (g, t) holds rows r = g + 8 (q & 1), logical k = 2t + 8 (q >> 1) + {0, 1}.
-template <int N>
-__device__ __forceinline__ void core16_setup(const EpochArgs &p, uint32_t *tab, float *cacc) {
-  for (int e = threadIdx.x; e < N * 128; e += blockDim.x) {
-    const int n = e >> 7, q = (e >> 5) & 3, lane = e & 31;
-    const int g = lane >> 2, t = lane & 3;
-    const int r = g + 8 * (q & 1);
-    const int k0 = 2 * t + 8 * (q >> 1);
-    const int j0 = phys_col16(k0), j1 = phys_col16(k0 + 1);
-    const float v0 = (j0 < p.J[n] && r < p.R) ? p.B[n][j0 * p.R + r] : 0.f;
-    const float v1 = (j1 < p.J[n] && r < p.R) ? p.B[n][j1 * p.R + r] : 0.f;
-    tab[e] = pack_bf16(v0, v1);
-  }
-  for (int e = threadIdx.x; e < N * CoreRegSmem<N>::ACC; e += blockDim.x) cacc[e] = 0.f;
-}
-
-// One tile of the register-resident core pass.  ab[n][u]: the lane's chunk of
-// the mode-n row of nonzero base + 8u + g, packed to bf16 (zeros for a masked
-// nonzero); xv[u][q]: the value of nonzero base + 8u + 2t + q.  Adds the
-// tile's G^T into the lane's Neumaier registers (gs, gc).
-template <int N>
-__device__ __forceinline__ void core16_tile(const EpochArgs &p, const uint32_t *tab, const uint32_t (&ab)[N][2][2],
-                                            const float (&xv)[2][2], int64_t base, float (&gs)[N][8],
-                                            float (&gc)[N][8], int lane) {
-  const int t = lane & 3;
-  // C^T per mode: ct[n][u][i], rows r = g + 8 (i >> 1), column m = 8u + 2t + (i & 1)
-  float ct[N][2][4];
-#pragma unroll
-  for (int n = 0; n < N; ++n) {
-    const uint32_t a0 = tab[(n * 4 + 0) * 32 + lane], a1 = tab[(n * 4 + 1) * 32 + lane];
-    const uint32_t a2 = tab[(n * 4 + 2) * 32 + lane], a3 = tab[(n * 4 + 3) * 32 + lane];
-#pragma unroll
-    for (int u = 0; u < 2; ++u) {
-      float acc[4] = {0.f, 0.f, 0.f, 0.f};
-      mma_bf16(acc, a0, a1, a2, a3, ab[n][u][0], ab[n][u][1]);
-#pragma unroll
-      for (int i = 0; i < 4; ++i) ct[n][u][i] = acc[i];
-    }
-  }
-  // xhat of the lane's nonzeros m = 8u + 2t + q, then (xhat - x)
-  float ne[2][2];
-#pragma unroll
-  for (int u = 0; u < 2; ++u)
-#pragma unroll
-    for (int q = 0; q < 2; ++q) {
-      float s0 = 1.f, s1 = 1.f;
-#pragma unroll
-      for (int n = 0; n < N; ++n) { s0 *= ct[n][u][q]; s1 *= ct[n][u][q + 2]; }
-      float sum = s0 + s1;
-      sum += __shfl_xor_sync(FULL, sum, 4);
-      sum += __shfl_xor_sync(FULL, sum, 8);
-      sum += __shfl_xor_sync(FULL, sum, 16);
-      const int64_t m = base + 8 * u + 2 * t + q;
-      ne[u][q] = m < p.end ? sum - xv[u][q] : 0.f;
-    }
-  const bool nonfinite = !isfinite(ne[0][0]) || !isfinite(ne[0][1]) || !isfinite(ne[1][0]) || !isfinite(ne[1][1]);
-  if (__any_sync(FULL, nonfinite) && lane == 0) atomicOr(p.err, ERRBIT_NONFINITE);
-#pragma unroll
-  for (int n = 0; n < N; ++n) {
-    // D^T as the A operand (k = the nonzeros)
-    float d[2][4];
-#pragma unroll
-    for (int u = 0; u < 2; ++u)
-#pragma unroll
-      for (int i = 0; i < 4; ++i) {
-        float pr = 1.f;
-#pragma unroll
-        for (int k = 0; k < N; ++k)
-          if (k != n) pr *= ct[k][u][i];
-        d[u][i] = pr;
-      }
-    const uint32_t da0 = pack_bf16(d[0][0], d[0][1]), da1 = pack_bf16(d[0][2], d[0][3]);
-    const uint32_t da2 = pack_bf16(d[1][0], d[1][1]), da3 = pack_bf16(d[1][2], d[1][3]);
-#pragma unroll
-    for (int v = 0; v < 2; ++v) {
-      // E (k = nonzeros, n = logical j = 8v + g)
-      const uint32_t e0 = scale_bf16x2(movmatrix_trans(ab[n][0][v]), ne[0][0], ne[0][1]);
-      const uint32_t e1 = scale_bf16x2(movmatrix_trans(ab[n][1][v]), ne[1][0], ne[1][1]);
-      float acc[4] = {0.f, 0.f, 0.f, 0.f};
-      mma_bf16(acc, da0, da1, da2, da3, e0, e1);
-#pragma unroll
-      for (int i = 0; i < 4; ++i) neumaier_add(gs[n][4 * v + i], gc[n][4 * v + i], acc[i]);
-    }
-  }
-}
-
-// CTA combine of the lanes' Neumaier registers in warp order, then the CTA
-// partial in the [n][K][K] layout of (sum, compensation) pairs.
-template <int N>
-__device__ __forceinline__ void core16_combine(const EpochArgs &p, float *cacc, const float (&gs)[N][8],
-                                               const float (&gc)[N][8], int lane) {
-  const int w = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  for (int ww = 0; ww < nw; ++ww) {
-    if (w == ww) {
-#pragma unroll
-      for (int n = 0; n < N; ++n)
-#pragma unroll
-        for (int i = 0; i < 8; ++i) {
-          float *cs = cacc + ((n * 2 + 0) * 8 + i) * 32 + lane;
-          float *cc = cacc + ((n * 2 + 1) * 8 + i) * 32 + lane;
-          float s = *cs, c = *cc;
-          neumaier_add(s, c, gs[n][i]);
-          *cs = s;
-          *cc = c + gc[n][i];
-        }
-    }
-    __syncthreads();
-  }
-  float *out = p.partial + size_t(blockIdx.x) * 2 * N * 16 * 16;
-  for (int e = threadIdx.x; e < N * 16 * 16; e += blockDim.x) {
-    out[2 * e] = 0.f;
-    out[2 * e + 1] = 0.f;
-  }
-  __syncthreads();
-  for (int e = threadIdx.x; e < N * 8 * 32; e += blockDim.x) {
-    const int n = e / 256, i = (e >> 5) & 7, ln = e & 31;
-    const int gg = ln >> 2, tt = ln & 3;
-    const int v = i >> 2, ii = i & 3;
-    const int r = gg + 8 * (ii >> 1);
-    const int j = phys_col16(8 * v + 2 * tt + (ii & 1));
-    const size_t o = (size_t(n) * 16 + j) * 16 + r;
-    out[2 * o] = cacc[((n * 2 + 0) * 8 + i) * 32 + ln];
-    out[2 * o + 1] = cacc[((n * 2 + 1) * 8 + i) * 32 + ln];
-  }
-}
-
-// ------------------------------- core phase, BF16 in registers, pipelined
-// The tile arithmetic above (core16_tile) with the row gathers moved off the
-// critical path of the warp: each warp keeps
-// a ring of CORE_STAGES tile buffers in shared memory and fills the buffer of
-// tile k + CORE_STAGES - 1 with asynchronous copies (cp.async, through L1)
-// while it computes tile k, so that every gather has CORE_STAGES - 1 tiles of
-// work to arrive instead of none.  A lane copies and later reads only its
-// own 16-byte chunk of each row; the tile's 16 values are copied by lanes
-// 0..15 and read by every lane after a warp barrier.  Masked nonzeros (past
-// the end, or with a coordinate outside [0, I_n), which latches
-// ERRBIT_INDEX) get zero-filled rows and values.
-constexpr int CORE_STAGES = 3;
-
-template <int N>
-struct CorePipeSmem {
-  static constexpr int ROWS = N * 2 * 32 * 16;         // bytes of one stage's rows: [n][u][lane] x 16 B
-  static constexpr int STAGE = ROWS + FT_TILE * 4;      // + the tile's values
-  static constexpr int WARP = CORE_STAGES * STAGE;
-  static constexpr int BASE = 4 * N * (CoreRegSmem<N>::TABW + CoreRegSmem<N>::ACC);  // tables, CTA sums
-  static constexpr size_t bytes(int warps) { return size_t(BASE) + size_t(warps) * WARP; }
-};
-
-__device__ __forceinline__ void cp_async16(uint32_t dst, const void *src, int src_bytes) {
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(src_bytes) : "memory");
-}
-__device__ __forceinline__ void cp_async4(uint32_t dst, const void *src, int src_bytes) {
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(dst), "l"(src), "r"(src_bytes) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-template <int PENDING>
-__device__ __forceinline__ void cp_async_wait() {
-  asm volatile("cp.async.wait_group %0;" ::"n"(PENDING) : "memory");
-}
-
-template <int N>
-__global__ void __launch_bounds__(256, N <= 3 ? 2 : 1) k_core_bf16p(const EpochArgs p) {
-  using L = CorePipeSmem<N>;
-  extern __shared__ __align__(16) float smem[];
-  uint32_t *tab = reinterpret_cast<uint32_t *>(smem);      // [N][4][32]
-  float *cacc = smem + N * CoreRegSmem<N>::TABW;            // [N][2][8][32]
-  core16_setup<N>(p, tab, cacc);
-  const int lane = threadIdx.x & 31;
-  const int g = lane >> 2, t = lane & 3;
-  unsigned char *ring = reinterpret_cast<unsigned char *>(smem) + L::BASE + (threadIdx.x >> 5) * L::WARP;
-  const uint32_t ring_s = static_cast<uint32_t>(__cvta_generic_to_shared(ring));
-  __syncthreads();
-
-  float gs[N][8], gc[N][8];
-#pragma unroll
-  for (int n = 0; n < N; ++n)
-#pragma unroll
-    for (int i = 0; i < 8; ++i) gs[n][i] = gc[n][i] = 0.f;
-
-  const int64_t warp = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
-  const int64_t nwarps = (int64_t(gridDim.x) * blockDim.x) >> 5;
-  const int64_t ntiles = (p.end - p.begin + FT_TILE - 1) / FT_TILE;
-
-  // coordinates of the next tile to fetch: rows m = base + 8u + g
-  int32_t nrow[N][2];
-  auto load_coords = [&](int64_t tile) {
-    const int64_t b = p.begin + tile * FT_TILE;
-#pragma unroll
-    for (int u = 0; u < 2; ++u)
-#pragma unroll
-      for (int n = 0; n < N; ++n) nrow[n][u] = (b + 8 * u + g < p.end) ? __ldcs(p.idx[n] + b + 8 * u + g) : 0;
-  };
-  // asynchronous copies of tile `tile` (coordinates in nrow) into ring stage s
-  auto fetch = [&](int64_t tile, int s) {
-    const int64_t b = p.begin + tile * FT_TILE;
-    const uint32_t st = ring_s + uint32_t(s * L::STAGE);
-    bool valid[2], bad = false;
-#pragma unroll
-    for (int u = 0; u < 2; ++u) {
-      valid[u] = b + 8 * u + g < p.end;
-      bool ok = true;
-#pragma unroll
-      for (int n = 0; n < N; ++n) ok = ok && nrow[n][u] >= 0 && int64_t(nrow[n][u]) < p.I[n];
-      if (valid[u] && !ok) { bad = true; valid[u] = false; }
-    }
-    if (bad) atomicOr(p.err, ERRBIT_INDEX);
-#pragma unroll
-    for (int n = 0; n < N; ++n) {
-      const int Jn = p.J[n];
-      const bool vec = ((p.vecmask >> n) & 1) != 0;
-#pragma unroll
-      for (int u = 0; u < 2; ++u) {
-        const uint32_t dst = st + uint32_t(((n * 2 + u) * 32 + lane) * 16);
-        const float *src = p.A[n] + int64_t(valid[u] ? nrow[n][u] : 0) * Jn + 4 * t;
-        if (vec) {
-          cp_async16(dst, valid[u] && 4 * t < Jn ? src : p.A[n], valid[u] && 4 * t < Jn ? 16 : 0);
-        } else {
-#pragma unroll
-          for (int q = 0; q < 4; ++q) {
-            const bool in = valid[u] && 4 * t + q < Jn;
-            cp_async4(dst + 4 * q, in ? src + q : p.A[n], in ? 4 : 0);
-          }
-        }
-      }
-    }
-    if (lane < FT_TILE) {
-      const bool in = b + lane < p.end;
-      cp_async4(st + uint32_t(L::ROWS + 4 * lane), in ? p.vals + b + lane : p.vals, in ? 4 : 0);
-    }
-  };
-
-  // prologue: stages 0 .. CORE_STAGES - 2 in flight, the coordinates of the
-  // tile after them in registers
-#pragma unroll
-  for (int s = 0; s < CORE_STAGES - 1; ++s) {
-    const int64_t tile = warp + int64_t(s) * nwarps;
-    if (tile < ntiles) {
-      load_coords(tile);
-      fetch(tile, s);
-    }
-    cp_async_commit();
-  }
-  {
-    const int64_t tile = warp + int64_t(CORE_STAGES - 1) * nwarps;
-    if (tile < ntiles) load_coords(tile);
-  }
-  int s_cur = 0;
-  for (int64_t tile = warp; tile < ntiles; tile += nwarps) {
-    // every lane is done with the stage that the next fetch overwrites
-    __syncwarp();
-    const int64_t ahead = tile + int64_t(CORE_STAGES - 1) * nwarps;
-    const int s_fill = s_cur == 0 ? CORE_STAGES - 1 : s_cur - 1;
-    if (ahead < ntiles) fetch(ahead, s_fill);
-    cp_async_commit();
-    if (ahead + nwarps < ntiles) load_coords(ahead + nwarps);
-    cp_async_wait<CORE_STAGES - 1>();
-    __syncwarp();
-    const unsigned char *st = ring + s_cur * L::STAGE;
-    uint32_t ab[N][2][2];
-#pragma unroll
-    for (int n = 0; n < N; ++n)
-#pragma unroll
-      for (int u = 0; u < 2; ++u) {
-        const float4 v = *reinterpret_cast<const float4 *>(st + ((n * 2 + u) * 32 + lane) * 16);
-        ab[n][u][0] = pack_bf16(v.x, v.y);
-        ab[n][u][1] = pack_bf16(v.z, v.w);
-      }
-    const float *xs = reinterpret_cast<const float *>(st + L::ROWS);
-    float xv[2][2];
-#pragma unroll
-    for (int u = 0; u < 2; ++u) {
-      const float2 x2 = *reinterpret_cast<const float2 *>(xs + 8 * u + 2 * t);
-      xv[u][0] = x2.x;
-      xv[u][1] = x2.y;
-    }
-    core16_tile<N>(p, tab, ab, xv, p.begin + tile * FT_TILE, gs, gc, lane);
-    s_cur = s_cur == CORE_STAGES - 1 ? 0 : s_cur + 1;
-  }
-  cp_async_wait<0>();
-  core16_combine<N>(p, cacc, gs, gc, lane);
-}
-
 // ------------------------------------ core phase, CTA-cooperative (BF16)
 // The core-gradient pass (Algorithm 5) for BF16 at padded rank K = 32, and at
 // K = 16 for orders whose per-lane state does not fit k_core_bf16p.  Since
@@ -1176,7 +883,8 @@ __device__ __forceinline__ void coop_store(unsigned char *dst, const uint32_t (&
   else *reinterpret_cast<uint2 *>(dst) = make_uint2(v[0], v[1]);
 }
 
-template <int N, int K>
+// STORE: the storage scheme (rows of C read from p.cst, Sec. 5.6).
+template <int N, int K, bool STORE = false>
 __global__ void __launch_bounds__(256, CoopSmem<N, K>::MINB) k_core_coop(const EpochArgs p) {
   using L = CoopSmem<N, K>;
   constexpr int CPL = K / 4;
@@ -1220,7 +928,8 @@ __global__ void __launch_bounds__(256, CoopSmem<N, K>::MINB) k_core_coop(const E
           for (int q = 0; q < CPL / 2; ++q) av[q] = pack_bf16(f.a[n][h][2 * q], f.a[n][h][2 * q + 1]);
           coop_store<CPL>(abuf + n * L::BUF + (FT_TILE * w + g + 8 * h) * L::LDB + 2 * CPL * t, av);
         }
-      f.compute(smem, TW, lane);
+      if constexpr (STORE) f.load_stored(p, lane);
+      else f.compute(smem, TW, lane);
       float ne[2];
 #pragma unroll
       for (int h = 0; h < 2; ++h) ne[h] = f.valid[h] ? f.xhat[h] - f.x[h] : 0.f;

@@ -36,20 +36,21 @@ ft::KernelSet make_set() {
   s.batch_core_smem = ft::CoreSmem<N, FT_K, FT_MATH>::bytes();
   s.batch_core_threads = 32 * ft::CoreSmem<N, FT_K, FT_MATH>::WARPS;
 #if FT_MATH == 2
-  // BF16: the CTA-cooperative core pass, except where the register-resident
-  // one below applies
+  s.core_store = reinterpret_cast<const void *>(&ft::k_core_coop<N, FT_K, true>);
+  s.core_store_smem = ft::CoopSmem<N, FT_K>::bytes();
+  s.core_store_threads = 32 * ft::CoopSmem<N, FT_K>::WARPS;
+#else
+  s.core_store = reinterpret_cast<const void *>(&ft::k_core<N, FT_K, FT_MATH, true>);
+  s.core_store_smem = ft::CoreSmem<N, FT_K, FT_MATH>::bytes();
+  s.core_store_threads = 32 * ft::CoreSmem<N, FT_K, FT_MATH>::WARPS;
+#endif
+#if FT_MATH == 2
+  // BF16: the CTA-cooperative core pass
   s.core = reinterpret_cast<const void *>(&ft::k_core_coop<N, FT_K>);
   s.core_smem = ft::CoopSmem<N, FT_K>::bytes();
   s.core_threads = 32 * ft::CoopSmem<N, FT_K>::WARPS;
 #endif
 #if FT_K == 16 && FT_MATH == 2
-  // BF16 at K = 16, N <= 3: the register-resident core pass with its row
-  // gathers pipelined through a per-warp shared-memory ring (8 warps per CTA)
-  if constexpr (N <= 3) {
-    s.core = reinterpret_cast<const void *>(&ft::k_core_bf16p<N>);
-    s.core_smem = ft::CorePipeSmem<N>::bytes(8);
-    s.core_threads = 256;
-  }
   if constexpr (N <= 4) {
     s.factor_tc = reinterpret_cast<const void *>(&ft::k_factor_tc<N>);
     s.factor_tc_smem = ft::tc::Smem<N>::bytes(0);

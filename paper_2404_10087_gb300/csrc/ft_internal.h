@@ -14,6 +14,10 @@ struct KernelSet {
   size_t factor_smem = 0;              // tables only; the hot-row cache adds to it
   size_t core_smem = 0;
   int core_threads = 256;
+  // core-gradient pass of the storage scheme (rows of C = A B precomputed)
+  const void *core_store = nullptr;
+  size_t core_store_smem = 0;
+  int core_store_threads = 256;
   // batched persistent kernels of this class (generic core, shared-memory staging)
   const void *batch_factor = nullptr;
   const void *batch_core = nullptr;

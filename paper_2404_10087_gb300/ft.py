@@ -24,6 +24,8 @@ PRECISIONS = {"fp32": FT_FP32, "tf32": FT_TF32, "bf16": FT_BF16}
 SCATTERS = {"hogwild": FT_HOGWILD, "deterministic": FT_DETERMINISTIC}
 FT_ENGINE_WARP, FT_ENGINE_TCGEN05 = 0, 1
 ENGINES = {"warp": FT_ENGINE_WARP, "tcgen05": FT_ENGINE_TCGEN05}
+FT_CORE_CALC, FT_CORE_STORE = 0, 1
+CORE_SCHEMES = {"calc": FT_CORE_CALC, "store": FT_CORE_STORE}
 
 FT_OK = 0
 STATUS = {0: "FT_OK", -1: "FT_ERR_ARG", -2: "FT_ERR_INDEX", -3: "FT_ERR_SHAPE", -4: "FT_ERR_CUDA",
@@ -31,7 +33,7 @@ STATUS = {0: "FT_OK", -1: "FT_ERR_ARG", -2: "FT_ERR_INDEX", -3: "FT_ERR_SHAPE", 
 
 # Every symbol the header declares (checked by the tests against the library).
 EXPORTS = ["ft_config_default", "ft_workspace_size", "ft_init", "ft_epoch_factors",
-           "ft_epoch_core", "ft_core_grad", "ft_predict", "ft_rmse", "ft_check",
+           "ft_epoch_core", "ft_epoch_core_sgd", "ft_permute", "ft_core_grad", "ft_predict", "ft_rmse", "ft_check",
            "ft_launch_count", "ft_destroy", "ft_status_str", "ft_core_grad_noalloc",
            "ft_batch_workspace_size", "ft_batch_init", "ft_batch_tune", "ft_batch_epoch",
            "ft_batch_rmse", "ft_batch_num_classes", "ft_batch_class_info", "ft_batch_launch_count",
@@ -55,7 +57,8 @@ class ft_config(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("scatter", ctypes.c_int),
                 ("det_batch", ctypes.c_int64), ("blocks_per_sm", ctypes.c_int),
                 ("hot_rows", ctypes.c_int), ("hot_window", ctypes.c_int),
-                ("hot_min_count", ctypes.c_int), ("engine", ctypes.c_int), ("reserved", ctypes.c_int * 3)]
+                ("hot_min_count", ctypes.c_int), ("engine", ctypes.c_int), ("core_scheme", ctypes.c_int),
+                ("reserved", ctypes.c_int * 2)]
 
 
 _lib = None
@@ -92,6 +95,8 @@ def _declare(lib):
         "ft_init": (INT, [_P, INT, _P, _P, INT, I64, _P, _P, _P, _P, _P, ctypes.c_size_t, _P, _P]),
         "ft_epoch_factors": (INT, [_P, FLT, FLT, _P, _P]),
         "ft_epoch_core": (INT, [_P, FLT, FLT, _P]),
+        "ft_epoch_core_sgd": (INT, [_P, FLT, FLT, I64, _P]),
+        "ft_permute": (INT, [_P, _P, _P, _P, _P]),
         "ft_core_grad": (INT, [_P, _P, _P]),
         "ft_predict": (INT, [_P, I64, _P, _P, _P]),
         "ft_rmse": (INT, [_P, I64, _P, _P, _P, _P]),
@@ -138,7 +143,8 @@ def _stream(stream) -> int:
 
 
 def make_config(precision="fp32", scatter="hogwild", det_batch=4096, blocks_per_sm=0,
-                hot_rows=None, hot_window=None, hot_min_count=None, engine="warp") -> ft_config:
+                hot_rows=None, hot_window=None, hot_min_count=None, engine="warp",
+                core_scheme="calc") -> ft_config:
     c = ft_config()
     load().ft_config_default(ctypes.byref(c))
     c.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
@@ -152,6 +158,7 @@ def make_config(precision="fp32", scatter="hogwild", det_batch=4096, blocks_per_
     if hot_min_count is not None:
         c.hot_min_count = int(hot_min_count)
     c.engine = ENGINES[engine] if isinstance(engine, str) else int(engine)
+    c.core_scheme = CORE_SCHEMES[core_scheme] if isinstance(core_scheme, str) else int(core_scheme)
     return c
 
 
@@ -188,6 +195,19 @@ def ft_epoch_factors(ctx, lr_a, lambda_a, row_step_scale=None, stream=None):
 
 def ft_epoch_core(ctx, lr_b, lambda_b, stream=None):
     _check(load().ft_epoch_core(ctx, float(lr_b), float(lambda_b), _stream(stream)), "ft_epoch_core")
+
+
+def ft_permute(ctx, perm, idx_out, vals_out, stream=None):
+    """perm: int32 device tensor (nnz,); idx_out: list of N int32 device
+    tensors (nnz,); vals_out: float32 device tensor (nnz,)."""
+    n = int(perm.numel())
+    _check(load().ft_permute(ctx, perm.data_ptr() if n else None, _ptrs(idx_out) if n else None,
+                             vals_out.data_ptr() if n else None, _stream(stream)), "ft_permute")
+
+
+def ft_epoch_core_sgd(ctx, lr_b, lambda_b, set_size, stream=None):
+    _check(load().ft_epoch_core_sgd(ctx, float(lr_b), float(lambda_b), int(set_size), _stream(stream)),
+           "ft_epoch_core_sgd")
 
 
 def ft_core_grad(ctx, G_out, stream=None):
@@ -252,7 +272,7 @@ class FastTuckerPlus:
 
     def __init__(self, idx, vals, A, B, precision="fp32", scatter="hogwild", det_batch=4096,
                  blocks_per_sm=0, stream=None, hot_rows=None, hot_window=None, hot_min_count=None,
-                 engine="warp"):
+                 engine="warp", core_scheme="calc"):
         N = len(A)
         if not (len(idx) == len(B) == N):
             raise ValueError("idx, A and B need one entry per mode")
@@ -268,7 +288,7 @@ class FastTuckerPlus:
         self.R = int(B[0].shape[1])
         self.nnz = int(vals.numel())
         self.cfg = make_config(precision, scatter, det_batch, blocks_per_sm, hot_rows, hot_window,
-                               hot_min_count, engine)
+                               hot_min_count, engine, core_scheme)
         ws = ft_workspace_size(self.I, self.J, self.R, self.nnz, self.cfg)
         self.workspace = torch.empty(max(ws, 256), dtype=torch.uint8, device=vals.device)
         self.ctx = ft_init(self.I, self.J, self.R, self.idx, vals, self.A, self.B, self.workspace,
@@ -279,6 +299,22 @@ class FastTuckerPlus:
 
     def epoch_core(self, lr, lam, stream=None):
         ft_epoch_core(self.ctx, lr, lam, stream)
+
+    def epoch_core_sgd(self, lr, lam, set_size, stream=None):
+        ft_epoch_core_sgd(self.ctx, lr, lam, set_size, stream)
+
+    def permute(self, perm, stream=None):
+        """Reorder the training nonzeros by perm (int32 device tensor).  The
+        reordered copies live in two buffers this object owns and alternates
+        between, so the caller's arrays are never overwritten."""
+        if not hasattr(self, "_spare"):
+            self._spare = [([torch.empty_like(t) for t in self.idx], torch.empty_like(self.vals))
+                           for _ in range(2)]
+            self._next = 0
+        idx_out, vals_out = self._spare[self._next]
+        ft_permute(self.ctx, perm, idx_out, vals_out, stream)
+        self.idx, self.vals = idx_out, vals_out
+        self._next ^= 1
 
     def core_grad(self, stream=None):
         G = torch.empty(sum(j * self.R for j in self.J), dtype=torch.float32, device=self.vals.device)

@@ -73,3 +73,15 @@ def test_engine_configuration_rejected_on_host():
         with pytest.raises(ft.FtError) as e:
             ft.ft_workspace_size(I, J, R, 100, cfg)
         assert e.value.status == -1, kw
+
+
+def test_core_scheme_configuration():
+    """The core phase's storage scheme is a config field (default:
+    calculation); unknown schemes are refused on the host."""
+    lib = ft.load()
+    cfg = ft.ft_config()
+    lib.ft_config_default(ctypes.byref(cfg))
+    assert cfg.core_scheme == ft.FT_CORE_CALC and list(cfg.reserved) == [0, 0]
+    with pytest.raises(ft.FtError) as e:
+        ft.ft_workspace_size((10, 10, 10), (16, 16, 16), 16, 100, ft.make_config(core_scheme=5))
+    assert e.value.status == -1

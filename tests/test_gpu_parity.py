@@ -132,13 +132,16 @@ def test_deterministic_factor_epoch(shape, precision):
         assert rel_fro(got[n] - A0[n], ref[n] - A0[n]) <= TOL_STEP[precision] * order_factor(precision, len(I)), n
 
 
+@pytest.mark.parametrize("scheme", ["calc", "store"])
 @pytest.mark.parametrize("precision", ["fp32", "tf32", "bf16"])
 @pytest.mark.parametrize("shape", SHAPES, ids=SHAPE_IDS)
-def test_core_gradient(shape, precision):
+def test_core_gradient(shape, precision, scheme):
+    """Both core schemes of Sec. 5.6: rows of C formed per nonzero
+    (calculation) or gathered from C = A B computed once in FP32 (storage)."""
     I, J, R, nnz = shape
     idx, x, A, B = synth.random_problem(3, I, J, R, nnz)
     gidx, gx, gA, gB = to_dev(idx, x, A, B)
-    m = ft.FastTuckerPlus(gidx, gx, gA, gB, precision=precision)
+    m = ft.FastTuckerPlus(gidx, gx, gA, gB, precision=precision, core_scheme=scheme)
     G = f64(m.core_grad())
     A64, B64, i64, x64 = f64(A), f64(B), idx.numpy(), x.double().numpy()
     ref = oracle.core_grad(A64, B64, i64, x64)
@@ -149,12 +152,13 @@ def test_core_gradient(shape, precision):
             assert rel_fro(G[n], ref[n]) <= 1e-5, n
 
 
-@pytest.mark.parametrize("precision", ["fp32", "bf16"])
-def test_core_epoch_and_errors(precision):
+@pytest.mark.parametrize("precision,scheme", [("fp32", "calc"), ("bf16", "calc"), ("fp32", "store"),
+                                              ("bf16", "store")])
+def test_core_epoch_and_errors(precision, scheme):
     I, J, R, nnz = (60, 70, 80), (16, 16, 16), 16, 5000
     idx, x, A, B = synth.random_problem(4, I, J, R, nnz)
     gidx, gx, gA, gB = to_dev(idx, x, A, B)
-    m = ft.FastTuckerPlus(gidx, gx, gA, gB, precision=precision)
+    m = ft.FastTuckerPlus(gidx, gx, gA, gB, precision=precision, core_scheme=scheme)
     lr, lam = 0.5, 0.01
     m.epoch_core(lr, lam)
     ref = oracle.core_epoch(f64(A), f64(B), idx.numpy(), x.double().numpy(), lr, lam)
@@ -167,6 +171,44 @@ def test_core_epoch_and_errors(precision):
     assert abs(r[0] - ro[0]) <= 1e-5 * ro[0]
     assert abs(r[1] - ro[1]) <= 1e-5 * ro[1]
     assert abs(r[2] - ro[2]) <= 2e-5 * ro[2]
+
+
+@pytest.mark.parametrize("scheme", ["calc", "store"])
+@pytest.mark.parametrize("precision", ["fp32", "bf16"])
+@pytest.mark.parametrize("shape", [SHAPES[0], SHAPES[4], SHAPES[1]], ids=[SHAPE_IDS[0], SHAPE_IDS[4], SHAPE_IDS[1]])
+def test_core_sgd_sets_match_oracle(shape, precision, scheme):
+    """Per-set core SGD (Algorithm 3's core loop): consecutive sets of S
+    nonzeros, a ragged last one, each an averaged core step from the core
+    matrices the previous set left."""
+    I, J, R, nnz = shape
+    idx, x, A, B = synth.random_problem(7, I, J, R, nnz)
+    gidx, gx, gA, gB = to_dev(idx, x, A, B)
+    m = ft.FastTuckerPlus(gidx, gx, gA, gB, precision=precision, core_scheme=scheme)
+    S = max(1, nnz // 5 + 3)
+    lr, lam = 0.5, 0.01
+    m.epoch_core_sgd(lr, lam, S)
+    m.check()
+    ref = oracle.core_epoch_sgd(f64(A), f64(B), idx.numpy(), x.double().numpy(), S, lr, lam)
+    got, B0 = f64(gB), f64(B)
+    for n in range(len(I)):
+        assert rel_fro(got[n] - B0[n], ref[n] - B0[n]) <= TOL_GRAD[precision] * order_factor(precision, len(I)), n
+
+
+def test_core_sgd_one_set_is_the_core_epoch():
+    """A set size of at least nnz is exactly Algorithm 5's step (bit for bit)."""
+    I, J, R, nnz = (40, 50, 60), (16, 16, 16), 16, 3000
+    idx, x, A, B = synth.random_problem(8, I, J, R, nnz)
+    gidx, gx, gA, gB = to_dev(idx, x, A, B)
+    gB2 = [b.clone() for b in gB]
+    m1 = ft.FastTuckerPlus(gidx, gx, gA, gB, precision="bf16")
+    m2 = ft.FastTuckerPlus(gidx, gx, gA, gB2, precision="bf16")
+    m1.epoch_core(0.3, 0.01)
+    m2.epoch_core_sgd(0.3, 0.01, nnz + 5)
+    torch.cuda.synchronize()
+    for a, b in zip(gB, gB2):
+        assert torch.equal(a, b)
+    with pytest.raises(ft.FtError):
+        m2.epoch_core_sgd(0.3, 0.01, 0)
 
 
 def test_row_step_scale_deterministic():
@@ -202,6 +244,67 @@ def test_hogwild_without_collisions_is_exact(precision, cache):
     ref = oracle.factor_epoch(f64(A), f64(B), idx.numpy(), x.double().numpy(), 1, 0.03, 0.02)
     for n in range(3):
         assert rel_fro(f64(gA)[n] - f64(A)[n], ref[n] - f64(A)[n]) <= TOL_STEP[precision]
+
+
+def test_permute_reorders_the_epoch():
+    """ft_permute (a reshuffle of Omega between iterations, Algorithm 3):
+    after reordering, the Hogwild pass (hot-row cache on, no row collisions,
+    so the result is exact) equals a fresh context built on the reordered
+    arrays bit for bit, and the oracle's sequential epoch in that order; a
+    second reshuffle writes into the other buffer and still matches."""
+    nnz = 16 * 40 + 7
+    I, J, R = (nnz + 3, nnz + 11, nnz + 2), (16, 16, 16), 16
+    g = torch.Generator().manual_seed(9)
+    idx = torch.stack([torch.randperm(In, generator=g)[:nnz] for In in I]).to(torch.int32)
+    _, x, A, B = synth.random_problem(9, I, J, R, nnz)
+    gidx, gx, gA, gB = to_dev(idx, x, A, B)
+    m = ft.FastTuckerPlus(gidx, gx, gA, gB, precision="fp32", hot_min_count=1)
+    order = torch.arange(nnz)
+    for k in range(2):
+        perm = torch.randperm(nnz, generator=g).to(torch.int32)
+        order = order[perm.long()]
+        m.permute(perm.to(DEV))
+        A_before = [a.clone() for a in gA]
+        m.epoch_factors(0.03, 0.02)
+        m.check()
+        pidx = idx[:, order]
+        px = x[order]
+        fresh_A = [a.clone() for a in A_before]
+        m2 = ft.FastTuckerPlus([t.contiguous().to(DEV) for t in pidx], px.contiguous().to(DEV), fresh_A,
+                               [b.clone() for b in gB], precision="fp32", hot_min_count=1)
+        m2.epoch_factors(0.03, 0.02)
+        torch.cuda.synchronize()
+        for a, b in zip(gA, fresh_A):
+            assert torch.equal(a, b), k
+        ref = oracle.factor_epoch(f64(A_before), f64(gB), pidx.numpy(), px.double().numpy(), 1, 0.03, 0.02)
+        for n in range(3):
+            assert rel_fro(f64(gA)[n], ref[n]) <= 1e-5
+    assert torch.equal(m.idx[0].cpu(), idx[0, order])
+
+
+def test_permute_deterministic_mode_and_bad_entries():
+    I, J, R, nnz = (30, 40, 50), (8, 16, 12), 10, 2000
+    idx, x, A, B = synth.random_problem(10, I, J, R, nnz)
+    gidx, gx, gA, gB = to_dev(idx, x, A, B)
+    m = ft.FastTuckerPlus(gidx, gx, gA, gB, precision="fp32", scatter="deterministic", det_batch=128)
+    g = torch.Generator().manual_seed(10)
+    perm = torch.randperm(nnz, generator=g).to(torch.int32)
+    m.permute(perm.to(DEV))
+    m.epoch_factors(0.02, 0.05)
+    m.check()
+    ref = oracle.factor_epoch(f64(A), f64(B), idx[:, perm.long()].numpy(), x[perm.long()].double().numpy(),
+                              128, 0.02, 0.05)
+    for n in range(3):
+        assert rel_fro(f64(gA)[n], ref[n]) <= 1e-4
+    bad = perm.clone()
+    bad[17] = nnz
+    m.permute(bad.to(DEV))
+    with pytest.raises(ft.FtError) as e:
+        m.check()
+    assert e.value.status == -2
+    with pytest.raises(ft.FtError) as e:
+        ft.ft_permute(m.ctx, perm.to(DEV), m.idx, m.vals)   # aliases the current arrays
+    assert e.value.status == -1
 
 
 def test_deterministic_mode_is_bitwise_reproducible():
