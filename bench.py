@@ -259,7 +259,7 @@ def run_ours(args, rank, world, local_rank):
 
     ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
 
-    def step(record=None):
+    def step(record=None, test=(tei, tex)):
         e0, e1, e2, e3 = (ev(), ev(), ev(), ev()) if record is not None else (None,) * 4
         if record is not None:
             e0.record(stream)
@@ -269,7 +269,7 @@ def run_ours(args, rank, world, local_rank):
         m.epoch_core(LR_B, LAM)
         if record is not None:
             e2.record(stream)
-        r = m.rmse(tei, tex)  # synchronises: the step's result reaches the host
+        r = m.rmse(*test)  # synchronises: the step's result reaches the host
         if record is not None:
             e3.record(stream)
             record.append((e0, e1, e2, e3))
@@ -299,23 +299,45 @@ def run_ours(args, rank, world, local_rank):
     c_ms = [b.elapsed_time(c) for _, b, c, _ in rec]
     r_ms = [c.elapsed_time(d) for _, _, c, d in rec]
 
-    # end to end through the C ABI with host buffers: every step copies the
-    # training COO from pinned host memory and reads the RMSE back
-    host_idx = [t.cpu().pin_memory() for t in tri]
-    host_x = trx.cpu().pin_memory()
-    h2d = sum(t.numel() * t.element_size() for t in host_idx) + host_x.numel() * 4
-    e2e_steps = max(1, min(args.steps, 5))
+    # end to end through the C ABI with host buffers: every step copies its
+    # inputs (the training and the test COO) from pinned host memory and
+    # reads the RMSE back.  Two device copies of the inputs alternate: while
+    # step k trains on one (after ft_rebind points the context at it), a
+    # second stream copies step k+1's inputs into the other.
+    host_in = [t.cpu().pin_memory() for t in list(tri) + [trx] + list(tei) + [tex]]
+    h2d = sum(t.numel() * t.element_size() for t in host_in)
+    e2e_steps = max(1, min(args.steps, 10))
+    dev_in = [list(tri) + [trx] + list(tei) + [tex], [torch.empty_like(t, device=dev) for t in host_in]]
+    bufs = [(d[:N], d[N], d[N + 1:2 * N + 1], d[2 * N + 1]) for d in dev_in]
+    copy_stream = torch.cuda.Stream(dev)
+    ready = [torch.cuda.Event(), torch.cuda.Event()]
+    free = [torch.cuda.Event(), torch.cuda.Event()]
+
+    def copy_in(k):
+        b = k % 2
+        with torch.cuda.stream(copy_stream):
+            copy_stream.wait_event(free[b])        # the step that last read buffer b is done
+            for dst, src in zip(dev_in[b], host_in):
+                dst.copy_(src, non_blocking=True)
+            ready[b].record(copy_stream)
+
     torch.cuda.synchronize()
     te0, te1 = ev(), ev()
     te0.record(stream)
-    for _ in range(e2e_steps):
-        for dst, src in zip(tri, host_idx):
-            dst.copy_(src, non_blocking=True)
-        trx.copy_(host_x, non_blocking=True)
-        step()
+    copy_stream.wait_stream(stream)
+    copy_in(0)
+    for k in range(e2e_steps):
+        b = k % 2
+        stream.wait_event(ready[b])
+        m.rebind(bufs[b][0], bufs[b][1])
+        if k + 1 < e2e_steps:
+            copy_in(k + 1)
+        step(test=(bufs[b][2], bufs[b][3]))
+        free[b].record(stream)
     te1.record(stream)
     torch.cuda.synchronize()
     e2e_ms = te0.elapsed_time(te1) / e2e_steps
+    m.rebind(tri, trx)
 
     (total_ms, e2e_ms), value = aggregate_replicas([total_ms, e2e_ms], nnz_train, args.steps, world, dev)
     ms_per_step = total_ms / args.steps
@@ -409,7 +431,10 @@ def run_sweep(args, local_rank):
     times (a) over the synthetic orders N = 3..10 (I = 10,000 per mode, 1e8
     uniform coordinates, J = R = 16), (b) over (R, J) in {16, 32}^2 on the
     Netflix-shaped Zipf tensor, (c) for the two core-phase schemes of
-    Sec. 5.6 (calculation vs storage) per precision on that tensor."""
+    Sec. 5.6 (calculation vs storage) per precision on that tensor, (d) for
+    the Algorithm 3 readings on that tensor: per-set core SGD and a reshuffle
+    of the nonzeros before every epoch, against Algorithm 5 in stored order
+    (core time, permutation time and the test-RMSE curve over 10 epochs)."""
     dev = torch.device(f"cuda:{local_rank}")
     torch.cuda.set_device(dev)
     ft.load()
@@ -464,6 +489,46 @@ def run_sweep(args, local_rank):
                 rows.append({"study": "core_scheme", "workload": w0.name, "precision": prec, "scheme": scheme,
                              "nnz_train": int(trx.numel()), "factor_ms": f, "core_ms": c})
                 m.close()
+    if args.sweep in ("variants", "all"):
+        # Algorithm 3 readings (per-set core SGD, reshuffle every iteration)
+        # on the Netflix-shaped tensor: 10 epochs from the same start
+        w0, tri, trx, tei, tex, A0, B0 = make_workload(dev, args.nnz, args.workload)
+        nnz = int(trx.numel())
+        epochs = 10
+        gen = torch.Generator(device=dev)
+        for variant, S, reshuffle in (("algorithm5", nnz, False), ("core_sgd", 10_000_000, False),
+                                      ("core_sgd", 1_000_000, False), ("reshuffle", nnz, True)):
+            gen.manual_seed(0)
+            A = [a.clone() for a in A0]
+            B = [b.clone() for b in B0]
+            m = ft.FastTuckerPlus(tri, trx, A, B, precision=args.precision, hot_rows=args.hot_rows,
+                                  hot_window=args.hot_window)
+            lr_b = LR_B * S / nnz   # the same total core movement per epoch
+            ms_core, ms_perm, curve = [], [], []
+            for _ in range(epochs):
+                if reshuffle:
+                    perm = torch.randperm(nnz, generator=gen, device=dev).to(torch.int32)
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    e0.record(stream)
+                    m.permute(perm)
+                    e1.record(stream)
+                    e1.synchronize()
+                    ms_perm.append(e0.elapsed_time(e1))
+                m.epoch_factors(LR, LAM)
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                if S >= nnz:
+                    m.epoch_core(LR_B, LAM)
+                else:
+                    m.epoch_core_sgd(lr_b, LAM, S)
+                e1.record(stream)
+                curve.append(round(m.rmse(tei, tex)[0], 5))
+                ms_core.append(e0.elapsed_time(e1))
+            rows.append({"study": "variant", "workload": w0.name, "variant": variant, "set_size": S,
+                         "lr_b": lr_b if S < nnz else LR_B, "core_ms": statistics.median(ms_core),
+                         "permute_ms": statistics.median(ms_perm) if ms_perm else None,
+                         "test_rmse_curve": curve})
+            m.close()
     return {"metric": METRIC, "unit": UNIT, "sweep": args.sweep, "precision": args.precision,
             "steps": args.steps, "warmup": args.warmup, "peak_hbm_gbs": peak, "peak_kind": peak_kind,
             "data": "synthetic", "rows": rows}
@@ -671,10 +736,11 @@ def main():
                          "precomputed once per core phase (Sec. 5.6)")
     ap.add_argument("--workload", default=WORKLOAD, choices=sorted(synth.WORKLOADS) + [BATCHED],
                     help="the timed tensor (default: the Netflix-shaped 1e8 Zipf tensor)")
-    ap.add_argument("--sweep", choices=["orders", "ranks", "schemes", "all"], default=None,
+    ap.add_argument("--sweep", choices=["orders", "ranks", "schemes", "variants", "all"], default=None,
                     help="instead of the headline line: the order sweep N = 3..10, the (R, J) "
-                         "sweep and/or the core-phase schemes (calculation vs storage) per "
-                         "precision, per-iteration phase times")
+                         "sweep, the core-phase schemes (calculation vs storage) per precision, "
+                         "and/or the Algorithm 3 variants (per-set core SGD, reshuffle every "
+                         "epoch); per-iteration phase times")
     ap.add_argument("--nnz", type=int, default=None,
                     help="distinct coordinates drawn (default: the workload's 1e8); "
                          "a smaller case of the same recipe, e.g. for profiling")

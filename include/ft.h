@@ -96,7 +96,7 @@ typedef struct {
    * refreshes its copy.  Only rows with at least hot_min_count training
    * nonzeros are cached.  hot_rows: -1 = as many as 96 KB hold, 0 = off. */
   int hot_rows;
-  int hot_window;      /* >= 1; default 64 */
+  int hot_window;      /* >= 1; default 128 */
   int hot_min_count;   /* >= 1; default 2 */
   /* Kernel family of the Hogwild factor pass: FT_ENGINE_WARP (default) = one
    * warp per 16-nonzero tile with mma.sync products; FT_ENGINE_TCGEN05 = one
@@ -120,7 +120,7 @@ enum { FT_ENGINE_WARP = 0, FT_ENGINE_TCGEN05 = 1 };
 enum { FT_CORE_CALC = 0, FT_CORE_STORE = 1 };
 
 /* Fill *cfg with the defaults: FT_FP32, FT_HOGWILD, det_batch 4096, automatic
- * grid, hot_rows -1, hot_window 64, hot_min_count 2, FT_ENGINE_WARP,
+ * grid, hot_rows -1, hot_window 128, hot_min_count 2, FT_ENGINE_WARP,
  * FT_CORE_CALC. */
 void ft_config_default(ft_config *cfg);
 
@@ -177,6 +177,20 @@ ft_status ft_epoch_core(ft_ctx *ctx, float lr_b, float lambda_b, void *stream);
 ft_status ft_permute(ft_ctx *ctx, const int32_t *perm, int32_t *const *idx_out, float *vals_out,
                      void *stream);
 
+/* Point the context at another copy of its training nonzeros: the same nnz,
+ * in any order, e.g. a buffer that an asynchronous host-to-device copy filled
+ * while the previous epoch ran (double buffering).  The arrays are borrowed
+ * from then on; the old ones are no longer read once the calls queued before
+ * this one have run.  The hot rows chosen at ft_init are kept and their
+ * coordinates are rebuilt on the device; in FT_DETERMINISTIC mode the row
+ * grouping is rebuilt on the host (synchronises); otherwise asynchronous.
+ * The new coordinates and values are not validated up front: the epoch
+ * kernels mask a coordinate outside [0, I_n) and latch FT_ERR_INDEX, and a
+ * non-finite value shows as a latched FT_ERR_NONFINITE (both reported by the
+ * next synchronising call).
+ *   idx   host array of N device pointers, nnz int32 each; vals: device */
+ft_status ft_rebind(ft_ctx *ctx, const int32_t *const *idx, const float *vals, void *stream);
+
 /* One core phase in the per-sample-set reading of Algorithm 3, whose core
  * loop applies rule "Update_FastTuckerPlus_core" for every sampled set Psi:
  * the training nonzeros are taken in stored order in consecutive sets of
@@ -204,7 +218,7 @@ ft_status ft_core_grad(ft_ctx *ctx, float *G_out, void *stream);
  *   receives G^(n) = sum (xhat - x) a^(n)T d^(n), each J_n x R row-major,
  *   concatenated over n.
  * Scratch: the call needs no workspace.  Its scratch (the per-CTA partial
- * sums of the core pass) lives in one 8 MiB device array compiled into the
+ * sums of the core pass) lives in one 16 MiB device array compiled into the
  * library, which every GPU that loads the library holds until the process
  * exits.  Calls that would need more than that (more CTAs times N * K * K
  * partials than fit) return FT_ERR_WORKSPACE; on a GB300 every supported

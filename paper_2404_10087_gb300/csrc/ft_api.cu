@@ -190,17 +190,20 @@ struct RemapArgs {
   const int32_t *idx[FT_MAXN];
   int32_t *out[FT_MAXN];
   const int32_t *slot_of[FT_MAXN];
+  int64_t I[FT_MAXN];
   int N;
   int64_t nnz;
 };
 
-// Coordinates of the Hogwild pass: a cached row becomes -(slot + 1).
+// Coordinates of the Hogwild pass: a cached row becomes -(slot + 1).  A
+// coordinate outside [0, I_n) is passed through unchanged (the epoch kernels
+// mask it and latch FT_ERR_INDEX).
 __global__ void k_remap(const RemapArgs a) {
   for (int64_t m = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; m < a.nnz;
        m += int64_t(gridDim.x) * blockDim.x)
     for (int n = 0; n < a.N; ++n) {
       const int32_t v = a.idx[n][m];
-      const int32_t sl = a.slot_of[n][v];
+      const int32_t sl = (v >= 0 && int64_t(v) < a.I[n]) ? a.slot_of[n][v] : -1;
       a.out[n][m] = sl >= 0 ? -(sl + 1) : v;
     }
 }
@@ -219,16 +222,40 @@ struct PermuteArgs {
   int *err;
 };
 
+// Each thread takes PERMUTE_U positions per round (strided by the grid, so
+// every access to perm and to the outputs stays coalesced) and issues all of
+// their random gathers before any store, to keep many loads in flight.
+constexpr int PERMUTE_U = 4;
+
 __global__ void k_permute(const PermuteArgs a) {
-  for (int64_t m = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; m < a.nnz;
-       m += int64_t(gridDim.x) * blockDim.x) {
-    int64_t q = a.perm[m];
-    if (q < 0 || q >= a.nnz) {
-      atomicOr(a.err, ft::ERRBIT_INDEX);
-      q = 0;
+  const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+  for (int64_t m0 = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; m0 < a.nnz; m0 += PERMUTE_U * stride) {
+    int64_t q[PERMUTE_U];
+    bool bad = false;
+#pragma unroll
+    for (int u = 0; u < PERMUTE_U; ++u) {
+      const int64_t m = m0 + u * stride;
+      q[u] = m < a.nnz ? int64_t(__ldcs(a.perm + m)) : 0;
+      if (q[u] < 0 || q[u] >= a.nnz) {
+        bad = bad || m < a.nnz;
+        q[u] = 0;
+      }
     }
-    for (int n = 0; n < a.N; ++n) a.out[n][m] = __ldg(a.idx[n] + q);
-    a.vals_out[m] = __ldg(a.vals + q);
+    if (bad) atomicOr(a.err, ft::ERRBIT_INDEX);
+    float v[PERMUTE_U];
+#pragma unroll
+    for (int u = 0; u < PERMUTE_U; ++u) v[u] = __ldg(a.vals + q[u]);
+#pragma unroll
+    for (int u = 0; u < PERMUTE_U; ++u)
+      if (m0 + u * stride < a.nnz) __stcs(a.vals_out + m0 + u * stride, v[u]);
+    for (int n = 0; n < a.N; ++n) {
+      int32_t c[PERMUTE_U];
+#pragma unroll
+      for (int u = 0; u < PERMUTE_U; ++u) c[u] = __ldg(a.idx[n] + q[u]);
+#pragma unroll
+      for (int u = 0; u < PERMUTE_U; ++u)
+        if (m0 + u * stride < a.nnz) __stcs(a.out[n] + m0 + u * stride, c[u]);
+    }
   }
 }
 
@@ -569,6 +596,7 @@ ft_status remap_hot(ft_ctx *c, cudaStream_t st) {
     ra.idx[n] = c->idx[n];
     ra.out[n] = ws_ptr<int32_t>(c, p.off_remap) + size_t(n) * p.nnz;
     ra.slot_of[n] = ws_ptr<int32_t>(c, p.off_counts) + off;
+    ra.I[n] = p.I[n];
     off += p.I[n];
   }
   ra.N = p.N;
@@ -673,7 +701,7 @@ void ft_config_default(ft_config *cfg) {
   cfg->det_batch = 4096;
   cfg->blocks_per_sm = 0;
   cfg->hot_rows = -1;
-  cfg->hot_window = 64;
+  cfg->hot_window = 128;
   cfg->hot_min_count = 2;
 }
 
@@ -895,13 +923,31 @@ ft_status ft_permute(ft_ctx *c, const int32_t *perm, int32_t *const *idx_out, fl
   a.N = p.N;
   a.nnz = p.nnz;
   a.err = ws_ptr<int>(c, p.off_err);
-  const int grid = int(std::min<int64_t>((p.nnz + 255) / 256, int64_t(p.num_sms) * 8));
+  const int grid = int(std::min<int64_t>((p.nnz + 255) / 256, int64_t(p.num_sms) * 16));
   ft_status s = launch(c, reinterpret_cast<const void *>(&k_permute), grid, 256, 0, &a, st);
   if (s != FT_OK) return s;
   for (int n = 0; n < p.N; ++n) c->idx[n] = idx_out[n];
   c->vals = vals_out;
   if (c->hot_active) {
     s = remap_hot(c, st);
+    if (s != FT_OK) return s;
+  }
+  if (p.cfg.scatter == FT_DETERMINISTIC) return build_segments(c, st);
+  return FT_OK;
+}
+
+ft_status ft_rebind(ft_ctx *c, const int32_t *const *idx, const float *vals, void *stream) {
+  if (!c) return FT_ERR_ARG;
+  const Plan &p = c->p;
+  if (p.nnz == 0) return FT_OK;
+  if (!idx || !vals) return FT_ERR_ARG;
+  for (int n = 0; n < p.N; ++n)
+    if (!idx[n]) return FT_ERR_ARG;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  for (int n = 0; n < p.N; ++n) c->idx[n] = idx[n];
+  c->vals = vals;
+  if (c->hot_active) {
+    const ft_status s = remap_hot(c, st);
     if (s != FT_OK) return s;
   }
   if (p.cfg.scatter == FT_DETERMINISTIC) return build_segments(c, st);
@@ -929,7 +975,7 @@ ft_status ft_core_grad(ft_ctx *c, float *G_out, void *stream) {
 // per-CTA (sum, compensation) partials of the core-gradient kernel.  It is a
 // file-scope device array, so every GPU that loads this library holds it
 // until the process exits, and every call shares it.
-#define FT_NOALLOC_SCRATCH_BYTES (8u << 20)
+#define FT_NOALLOC_SCRATCH_BYTES (16u << 20)
 static __device__ __align__(256) unsigned char g_noalloc_scratch[FT_NOALLOC_SCRATCH_BYTES];
 
 namespace {

@@ -36,7 +36,11 @@
 
 namespace ft {
 
-enum Math { MATH_FP32 = 0, MATH_TF32 = 1, MATH_BF16 = 2 };
+// MATH_TF32X3: FP32-accurate products on the TF32 tensor cores, each operand
+// split into a TF32 head and a TF32 tail (x = hi + lo) and the product taken
+// as lo.hi + hi.lo + hi.hi (the lo.lo term, ~2^-22 relative, is dropped);
+// used by the prediction and error passes.
+enum Math { MATH_FP32 = 0, MATH_TF32 = 1, MATH_BF16 = 2, MATH_TF32X3 = 3 };
 
 // Latched device error bits (workspace word 0).
 enum : int { ERRBIT_NONFINITE = 1, ERRBIT_INDEX = 2, ERRBIT_VALUE = 4, ERRBIT_TIMEOUT = 8 };
@@ -207,6 +211,57 @@ struct Prod<K, MATH_TF32> {
       for (int s = 0; s < KS; ++s) {
         const uint2 b = tab[(u * KS + s) * 32 + lane];
         mma_tf32(acc, xa[0][2 * s], xa[1][2 * s], xa[0][2 * s + 1], xa[1][2 * s + 1], b.x, b.y);
+      }
+      y[0][2 * u] = acc[0]; y[0][2 * u + 1] = acc[1];
+      y[1][2 * u] = acc[2]; y[1][2 * u + 1] = acc[3];
+    }
+  }
+};
+
+// Three-pass TF32 (MATH_TF32X3) with the layout of Prod<K, MATH_TF32>: the
+// table holds the head and the tail of every B fragment.
+template <int K>
+struct Prod<K, MATH_TF32X3> {
+  static constexpr int CPL = K / 4;
+  static constexpr int NT = K / 8;
+  static constexpr int KS = K / 8;
+  static constexpr int WORDS = NT * KS * 32 * 4;
+  __device__ static void split(float v, uint32_t &hi, uint32_t &lo) {
+    hi = to_tf32(v);
+    lo = to_tf32(v - __uint_as_float(hi));
+  }
+  __device__ static void fill(float *tabf, const float *__restrict__ Bn, int J, int R, int which) {
+    uint32_t *tab = reinterpret_cast<uint32_t *>(tabf);
+    for (int e = threadIdx.x; e < NT * KS * 32; e += blockDim.x) {
+      const int lane = e & 31, us = e >> 5, s = us % KS, u = us / KS;
+      const int g = lane >> 2, t = lane & 3;
+      const int col = out_col<K>(u, g);
+      const int k0 = CPL * t + 2 * s;
+      split(core_entry(Bn, J, R, which, k0, col), tab[4 * e], tab[4 * e + 2]);
+      split(core_entry(Bn, J, R, which, k0 + 1, col), tab[4 * e + 1], tab[4 * e + 3]);
+    }
+  }
+  __device__ static void run(const float (&x)[2][CPL], const float *tabf, float (&y)[2][CPL], int lane) {
+    const uint4 *tab = reinterpret_cast<const uint4 *>(tabf);
+    uint32_t xh[2][CPL], xl[2][CPL];
+#pragma unroll
+    for (int q = 0; q < CPL; ++q) {
+      split(x[0][q], xh[0][q], xl[0][q]);
+      split(x[1][q], xh[1][q], xl[1][q]);
+    }
+#pragma unroll
+    for (int u = 0; u < NT; ++u) {
+      float acc[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+      for (int s = 0; s < KS; ++s) {
+        const uint4 b = tab[(u * KS + s) * 32 + lane];
+        mma_tf32(acc, xl[0][2 * s], xl[1][2 * s], xl[0][2 * s + 1], xl[1][2 * s + 1], b.x, b.y);
+        mma_tf32(acc, xh[0][2 * s], xh[1][2 * s], xh[0][2 * s + 1], xh[1][2 * s + 1], b.z, b.w);
+      }
+#pragma unroll
+      for (int s = 0; s < KS; ++s) {
+        const uint4 b = tab[(u * KS + s) * 32 + lane];
+        mma_tf32(acc, xh[0][2 * s], xh[1][2 * s], xh[0][2 * s + 1], xh[1][2 * s + 1], b.x, b.y);
       }
       y[0][2 * u] = acc[0]; y[0][2 * u + 1] = acc[1];
       y[1][2 * u] = acc[2]; y[1][2 * u + 1] = acc[3];
@@ -855,17 +910,76 @@ __global__ void __launch_bounds__(256) k_core(const EpochArgs p) {
 //            block into Neumaier (sum, compensation) registers.
 // Every output element has exactly one owning warp, so the CTA partial needs
 // no combine; fixed grid and tile order make the pass reproducible bit for bit.
+__device__ __forceinline__ void ldsm_x4(uint32_t addr, uint32_t &r0, uint32_t &r1, uint32_t &r2, uint32_t &r3) {
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0, %1, %2, %3}, [%4];"
+               : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
+               : "r"(addr)
+               : "memory");
+}
+
+// C = A_Psi B^(n) for a warp's 16 staged BF16 rows (A operand by ldmatrix,
+// natural contraction order), accumulators in the row-chunk layout of
+// Prod: y[h][q] is row g + 8h, column r = (K/4) t + q.  The B table holds,
+// per n-tile u and k-step s, the lane's (b0, b1) = B rows 16s + 2t (+1) and
+// 16s + 2t + 8 (+9) of the output column out_col(u, g) (zero outside
+// J_n x R).  The same BF16 roundings as Prod<K, MATH_BF16>.
+template <int K>
+struct CoopProd {
+  static constexpr int NT = K / 8;
+  static constexpr int KS = K / 16;
+  static constexpr int WORDS = NT * KS * 32 * 2;
+  __device__ static void fill(float *tabf, const float *__restrict__ Bn, int J, int R) {
+    uint32_t *tab = reinterpret_cast<uint32_t *>(tabf);
+    for (int e = threadIdx.x; e < NT * KS * 32; e += blockDim.x) {
+      const int lane = e & 31, us = e >> 5, s = us % KS, u = us / KS;
+      const int g = lane >> 2, t = lane & 3;
+      const int col = out_col<K>(u, g);
+      const int k0 = 16 * s + 2 * t;
+      tab[2 * e] = pack_bf16(core_entry(Bn, J, R, 0, k0, col), core_entry(Bn, J, R, 0, k0 + 1, col));
+      tab[2 * e + 1] = pack_bf16(core_entry(Bn, J, R, 0, k0 + 8, col), core_entry(Bn, J, R, 0, k0 + 9, col));
+    }
+  }
+  // rows_s: shared address of the warp's first staged row; ldb: row stride
+  __device__ static void run(uint32_t rows_s, int ldb, const float *tabf, float (&y)[2][K / 4], int lane) {
+    const uint2 *tab = reinterpret_cast<const uint2 *>(tabf);
+    const int ri = lane & 7, q = lane >> 3;
+    uint32_t a[KS][4];
+#pragma unroll
+    for (int s = 0; s < KS; ++s)
+      ldsm_x4(rows_s + (ri + 8 * (q & 1)) * ldb + 2 * (16 * s + 8 * (q >> 1)), a[s][0], a[s][1], a[s][2],
+              a[s][3]);
+#pragma unroll
+    for (int u = 0; u < NT; ++u) {
+      float acc[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+      for (int s = 0; s < KS; ++s) {
+        const uint2 b = tab[(u * KS + s) * 32 + lane];
+        mma_bf16(acc, a[s][0], a[s][1], a[s][2], a[s][3], b.x, b.y);
+      }
+      y[0][2 * u] = acc[0]; y[0][2 * u + 1] = acc[1];
+      y[1][2 * u] = acc[2]; y[1][2 * u + 1] = acc[3];
+    }
+  }
+};
+
 template <int N, int K>
 struct CoopSmem {
   static constexpr int WARPS = 8;
   static constexpr int ROWS = WARPS * FT_TILE;              // nonzeros per CTA tile
   static constexpr int LDB = 2 * K + 16;                    // bytes per staged row (conflict-free ldmatrix)
   static constexpr int BUF = ROWS * LDB;                    // bytes of one [ROWS][K] bf16 buffer
-  static constexpr int TW = Prod<K, MATH_BF16>::WORDS;
+  static constexpr int TW = CoopProd<K>::WORDS;             // == Prod<K, MATH_BF16>::WORDS
   static constexpr int TAB = N * TW * 4;                    // a.B operand tables
   static constexpr int UNITS = N * (K / 16) * (K / 16);     // 16 x 16 output blocks
   static constexpr int UPW = (UNITS + WARPS - 1) / WARPS;   // blocks per warp
-  static constexpr int MINB = (K == 16 && N <= 5) ? 2 : 1;  // CTAs per SM the registers allow
+  // A_SMEM: form C = A_Psi B from the staged BF16 rows (ldmatrix) instead of
+  // the gathered registers.  It frees the registers that let two CTAs share
+  // an SM at (K, N) = (16, 6) and (32, 3); elsewhere it measured 3-4% slower.
+  static constexpr bool A_SMEM = (K == 16 && N == 6) || (K == 32 && N == 3);
+  // CTAs per SM (the launch bound caps the registers to fit them): three at
+  // K = 16, N <= 3 (75 registers, no spills), two up to N = 6 and at K = 32,
+  // N = 3, else one
+  static constexpr int MINB = (K == 16 && N <= 3) ? 3 : ((K == 16 && N <= 6) || (K == 32 && N == 3)) ? 2 : 1;
   static constexpr size_t bytes() { return size_t(TAB) + size_t(2) * N * BUF; }
 };
 
@@ -887,6 +1001,7 @@ __device__ __forceinline__ void coop_store(unsigned char *dst, const uint32_t (&
 template <int N, int K, bool STORE = false>
 __global__ void __launch_bounds__(256, CoopSmem<N, K>::MINB) k_core_coop(const EpochArgs p) {
   using L = CoopSmem<N, K>;
+  static_assert(CoopProd<K>::WORDS == Prod<K, MATH_BF16>::WORDS, "one table size for both C paths");
   constexpr int CPL = K / 4;
   constexpr int TW = L::TW;
   extern __shared__ __align__(16) float smem[];
@@ -895,7 +1010,12 @@ __global__ void __launch_bounds__(256, CoopSmem<N, K>::MINB) k_core_coop(const E
   unsigned char *dbuf = abuf + N * L::BUF;                  // [N][ROWS] rows of (xhat - x) D^(n)
   const uint32_t abuf_s = static_cast<uint32_t>(__cvta_generic_to_shared(abuf));
   const uint32_t dbuf_s = static_cast<uint32_t>(__cvta_generic_to_shared(dbuf));
-  fill_tables<N, K, MATH_BF16>(smem, p, false);
+  if constexpr (L::A_SMEM) {
+#pragma unroll 1
+    for (int n = 0; n < N; ++n) CoopProd<K>::fill(smem + n * TW, p.B[n], p.J[n], p.R);
+  } else {
+    fill_tables<N, K, MATH_BF16>(smem, p, false);
+  }
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int g = lane >> 2, t = lane & 3;
 
@@ -917,8 +1037,8 @@ __global__ void __launch_bounds__(256, CoopSmem<N, K>::MINB) k_core_coop(const E
     {
       Front<N, K, MATH_BF16, true> f;
       f.gather(p, cur, lane);
-      // the raw rows go to shared memory first, so that they need no
-      // registers after C is formed
+      // the raw rows go to shared memory as BF16 right away (the operand of
+      // both products), so that they need no registers afterwards
 #pragma unroll
       for (int n = 0; n < N; ++n)
 #pragma unroll
@@ -928,8 +1048,17 @@ __global__ void __launch_bounds__(256, CoopSmem<N, K>::MINB) k_core_coop(const E
           for (int q = 0; q < CPL / 2; ++q) av[q] = pack_bf16(f.a[n][h][2 * q], f.a[n][h][2 * q + 1]);
           coop_store<CPL>(abuf + n * L::BUF + (FT_TILE * w + g + 8 * h) * L::LDB + 2 * CPL * t, av);
         }
-      if constexpr (STORE) f.load_stored(p, lane);
-      else f.compute(smem, TW, lane);
+      if constexpr (STORE) {
+        f.load_stored(p, lane);
+      } else if constexpr (L::A_SMEM) {
+        __syncwarp();
+#pragma unroll
+        for (int n = 0; n < N; ++n)
+          CoopProd<K>::run(abuf_s + n * L::BUF + FT_TILE * w * L::LDB, L::LDB, smem + n * TW, f.c[n], lane);
+        f.predict();
+      } else {
+        f.compute(smem, TW, lane);
+      }
       float ne[2];
 #pragma unroll
       for (int h = 0; h < 2; ++h) ne[h] = f.valid[h] ? f.xhat[h] - f.x[h] : 0.f;
@@ -1006,13 +1135,14 @@ __global__ void __launch_bounds__(256, CoopSmem<N, K>::MINB) k_core_coop(const E
 }
 
 // ----------------------------------------------------- predict and errors
-// FP32 predictions on the CUDA cores (the tensor-core modes only change the
-// epochs).  MODE 0: write xhat; MODE 1: per-CTA float64 sums of e^2 and |e|.
+// FP32-accurate predictions (three-pass TF32 products; the precision of the
+// epochs does not apply here).  MODE 0: write xhat; MODE 1: per-CTA float64
+// sums of e^2 and |e|.
 template <int N, int K, int MODE>
 __global__ void __launch_bounds__(256) k_eval(const EpochArgs p) {
   extern __shared__ __align__(16) float smem[];
-  constexpr int TW = Prod<K, MATH_FP32>::WORDS;
-  fill_tables<N, K, MATH_FP32>(smem, p, false);
+  constexpr int TW = Prod<K, MATH_TF32X3>::WORDS;
+  fill_tables<N, K, MATH_TF32X3>(smem, p, false);
   __shared__ double red[2][8];
   __syncthreads();
   const int lane = threadIdx.x & 31;
@@ -1021,7 +1151,7 @@ __global__ void __launch_bounds__(256) k_eval(const EpochArgs p) {
   const int64_t ntiles = (p.end - p.begin + FT_TILE - 1) / FT_TILE;
   double se = 0.0, ae = 0.0;
   for (int64_t tile = warp; tile < ntiles; tile += nwarps) {
-    Front<N, K, MATH_FP32, true> f;
+    Front<N, K, MATH_TF32X3, true> f;
     f.load(p, p.begin + tile * FT_TILE, lane, MODE == 1);
     f.compute(smem, TW, lane);
     if ((lane & 3) == 0) {

@@ -1,4 +1,5 @@
-// Explicit instantiations of the FP32 prediction / error kernels for one
+// Explicit instantiations of the prediction / error kernels (FP32-accurate
+// three-pass TF32 products) and the row-statistics kernels for one
 // padded rank K (built with FT_K in {16, 32}).
 #include "ft_device.cuh"
 #include "ft_internal.h"
@@ -16,10 +17,10 @@ ft::EvalSet make_eval() {
   ft::EvalSet s;
   s.predict = reinterpret_cast<const void *>(&ft::k_eval<N, FT_K, 0>);
   s.errors = reinterpret_cast<const void *>(&ft::k_eval<N, FT_K, 1>);
-  s.smem = size_t(N) * ft::Prod<FT_K, ft::MATH_FP32>::WORDS * sizeof(float);
+  s.smem = size_t(N) * ft::Prod<FT_K, ft::MATH_TF32X3>::WORDS * sizeof(float);
   s.row_stats1 = reinterpret_cast<const void *>(&ft::k_row_stats<N, FT_K, 1>);
   s.row_stats2 = reinterpret_cast<const void *>(&ft::k_row_stats<N, FT_K, 2>);
-  s.stats_smem = 2 * s.smem;
+  s.stats_smem = 2 * size_t(N) * ft::Prod<FT_K, ft::MATH_FP32>::WORDS * sizeof(float);
   return s;
 }
 }  // namespace

@@ -33,7 +33,7 @@ STATUS = {0: "FT_OK", -1: "FT_ERR_ARG", -2: "FT_ERR_INDEX", -3: "FT_ERR_SHAPE", 
 
 # Every symbol the header declares (checked by the tests against the library).
 EXPORTS = ["ft_config_default", "ft_workspace_size", "ft_init", "ft_epoch_factors",
-           "ft_epoch_core", "ft_epoch_core_sgd", "ft_permute", "ft_core_grad", "ft_predict", "ft_rmse", "ft_check",
+           "ft_epoch_core", "ft_epoch_core_sgd", "ft_permute", "ft_rebind", "ft_core_grad", "ft_predict", "ft_rmse", "ft_check",
            "ft_launch_count", "ft_destroy", "ft_status_str", "ft_core_grad_noalloc",
            "ft_batch_workspace_size", "ft_batch_init", "ft_batch_tune", "ft_batch_epoch",
            "ft_batch_rmse", "ft_batch_num_classes", "ft_batch_class_info", "ft_batch_launch_count",
@@ -97,6 +97,7 @@ def _declare(lib):
         "ft_epoch_core": (INT, [_P, FLT, FLT, _P]),
         "ft_epoch_core_sgd": (INT, [_P, FLT, FLT, I64, _P]),
         "ft_permute": (INT, [_P, _P, _P, _P, _P]),
+        "ft_rebind": (INT, [_P, _P, _P, _P]),
         "ft_core_grad": (INT, [_P, _P, _P]),
         "ft_predict": (INT, [_P, I64, _P, _P, _P]),
         "ft_rmse": (INT, [_P, I64, _P, _P, _P, _P]),
@@ -205,6 +206,13 @@ def ft_permute(ctx, perm, idx_out, vals_out, stream=None):
                              vals_out.data_ptr() if n else None, _stream(stream)), "ft_permute")
 
 
+def ft_rebind(ctx, idx, vals, stream=None):
+    """idx: list of N int32 device tensors (nnz,); vals: float32 (nnz,)."""
+    n = int(vals.numel())
+    _check(load().ft_rebind(ctx, _ptrs(idx) if n else None, vals.data_ptr() if n else None, _stream(stream)),
+           "ft_rebind")
+
+
 def ft_epoch_core_sgd(ctx, lr_b, lambda_b, set_size, stream=None):
     _check(load().ft_epoch_core_sgd(ctx, float(lr_b), float(lambda_b), int(set_size), _stream(stream)),
            "ft_epoch_core_sgd")
@@ -302,6 +310,16 @@ class FastTuckerPlus:
 
     def epoch_core_sgd(self, lr, lam, set_size, stream=None):
         ft_epoch_core_sgd(self.ctx, lr, lam, set_size, stream)
+
+    def rebind(self, idx, vals, stream=None):
+        """Train on another copy of the nonzeros from now on (same nnz)."""
+        if len(idx) != len(self.idx) or int(vals.numel()) != self.nnz:
+            raise ValueError("rebind needs N coordinate arrays and nnz values")
+        for t in list(idx) + [vals]:
+            if not t.is_cuda or not t.is_contiguous():
+                raise ValueError("every tensor must be a contiguous CUDA tensor")
+        ft_rebind(self.ctx, idx, vals, stream)
+        self.idx, self.vals = list(idx), vals
 
     def permute(self, perm, stream=None):
         """Reorder the training nonzeros by perm (int32 device tensor).  The

@@ -282,6 +282,40 @@ def test_permute_reorders_the_epoch():
     assert torch.equal(m.idx[0].cpu(), idx[0, order])
 
 
+def test_rebind_to_another_copy():
+    """ft_rebind: after pointing the context at a copy of its nonzeros (and
+    spoiling the old arrays) the Hogwild pass (hot-row cache on, no row
+    collisions) equals a fresh context on the copy bit for bit; a bad
+    coordinate in a rebound array is masked and reported."""
+    nnz = 16 * 30 + 5
+    I, J, R = (nnz + 3, nnz + 7, nnz + 1), (16, 16, 16), 16
+    g = torch.Generator().manual_seed(11)
+    idx = torch.stack([torch.randperm(In, generator=g)[:nnz] for In in I]).to(torch.int32)
+    _, x, A, B = synth.random_problem(11, I, J, R, nnz)
+    gidx, gx, gA, gB = to_dev(idx, x, A, B)
+    m = ft.FastTuckerPlus(gidx, gx, gA, gB, precision="bf16", hot_min_count=1)
+    cidx, cx = [t.clone() for t in gidx], gx.clone()
+    m.rebind(cidx, cx)
+    for t in gidx:
+        t.fill_(-1)
+    gx.fill_(float("nan"))
+    fresh = [a.clone() for a in gA]
+    m.epoch_factors(0.03, 0.02)
+    m.check()
+    m2 = ft.FastTuckerPlus(cidx, cx, fresh, [b.clone() for b in gB], precision="bf16", hot_min_count=1)
+    m2.epoch_factors(0.03, 0.02)
+    torch.cuda.synchronize()
+    for a, b in zip(gA, fresh):
+        assert torch.equal(a, b)
+    bad = [t.clone() for t in cidx]
+    bad[1][3] = I[1]
+    m.rebind(bad, cx)
+    m.epoch_factors(0.03, 0.02)
+    with pytest.raises(ft.FtError) as e:
+        m.check()
+    assert e.value.status == -2
+
+
 def test_permute_deterministic_mode_and_bad_entries():
     I, J, R, nnz = (30, 40, 50), (8, 16, 12), 10, 2000
     idx, x, A, B = synth.random_problem(10, I, J, R, nnz)

@@ -63,6 +63,19 @@ def test_no_alloc_core_grad_matches_context_path(precision, tol):
         assert rel_fro(got, ref) <= tol
 
 
+@pytest.mark.parametrize("precision", ["fp32", "tf32", "bf16"])
+def test_no_alloc_fits_the_largest_shapes(precision):
+    """The scratch array holds the partials of every supported shape at the
+    grid the context path uses (the largest per-CTA partials: N * K * K at
+    K = 32, N = 3..5, and at K = 16, N = 6..10)."""
+    for I, J, R in (((9, 10, 11, 12, 13), (32,) * 5, 32), ((9, 10, 11, 12), (32,) * 4, 32),
+                    ((9, 10, 11), (32,) * 3, 32), ((5,) * 10, (16,) * 10, 16), ((6,) * 6, (16,) * 6, 16)):
+        inputs = problem(24, I, J, R, 16 * 7 + 5)
+        ref = with_context(*inputs, precision)
+        got = no_alloc(*inputs, precision)
+        assert rel_fro(got, ref) <= 1e-5, (len(I), J[0])
+
+
 def test_no_alloc_reports_bad_coordinates():
     idx, x, A, B = problem(23, (10, 11, 12), (4, 4, 4), 4, 100)
     bad = [t.clone() for t in idx]
