@@ -113,7 +113,17 @@ typedef struct {
    * storage scheme faster on CUDA cores and calculation faster with tensor
    * cores.  Both give the same gradient up to rounding. */
   int core_scheme;
-  int reserved[2];     /* must be zero */
+  /* 1: keep the factor matrices in L2 while other traffic streams through
+   * it (for example a host-to-device copy of the next epoch's nonzeros that
+   * overlaps this epoch): every launch of the context carries an access-policy
+   * window over the address span of A^(0..N-1), marked persisting.  ft_init
+   * raises the calling process's persisting-L2 limit (cudaLimitPersistingL2CacheSize
+   * of the current device, a per-process setting) to the window size, capped
+   * at the device maximum, if it is lower.  Place the factor matrices in one
+   * allocation so that the span covers nothing else.  A cache hint only:
+   * results are unchanged.  0 (default): off. */
+  int l2_persist;
+  int reserved[1];     /* must be zero */
 } ft_config;
 
 enum { FT_ENGINE_WARP = 0, FT_ENGINE_TCGEN05 = 1 };
@@ -121,7 +131,7 @@ enum { FT_CORE_CALC = 0, FT_CORE_STORE = 1 };
 
 /* Fill *cfg with the defaults: FT_FP32, FT_HOGWILD, det_batch 4096, automatic
  * grid, hot_rows -1, hot_window 128, hot_min_count 2, FT_ENGINE_WARP,
- * FT_CORE_CALC. */
+ * FT_CORE_CALC, l2_persist 0. */
 void ft_config_default(ft_config *cfg);
 
 /* Bytes of device workspace needed by ft_init for this problem (host call;

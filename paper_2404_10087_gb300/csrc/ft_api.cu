@@ -368,8 +368,8 @@ ft_status make_plan(int N, const int64_t *I, const int *J, int R, int64_t nnz, c
   if (c.scatter == FT_DETERMINISTIC && c.det_batch < 1) return FT_ERR_ARG;
   if (c.blocks_per_sm < 0) return FT_ERR_ARG;
   if (c.hot_rows < -1 || c.hot_window < 1 || c.hot_min_count < 1) return FT_ERR_ARG;
-  for (int q = 0; q < 2; ++q)
-    if (c.reserved[q] != 0) return FT_ERR_ARG;
+  if (c.reserved[0] != 0) return FT_ERR_ARG;
+  if (c.l2_persist != 0 && c.l2_persist != 1) return FT_ERR_ARG;
   if (c.core_scheme != FT_CORE_CALC && c.core_scheme != FT_CORE_STORE) return FT_ERR_ARG;
   if (c.engine != FT_ENGINE_WARP && c.engine != FT_ENGINE_TCGEN05) return FT_ERR_ARG;
   if (c.engine == FT_ENGINE_TCGEN05 && (c.scatter != FT_HOGWILD || c.precision != FT_BF16)) return FT_ERR_ARG;
@@ -492,6 +492,10 @@ struct ft_ctx {
   int hot_base[FT_MAXN + 1] = {0};       // cache slots of mode n: [base[n], base[n+1])
   bool hot_active = false;
   int64_t launches = 0;
+  // l2_persist: the access-policy window over the factor matrices that every
+  // launch of this context carries
+  bool l2_on = false;
+  cudaAccessPolicyWindow l2_window{};
 };
 
 namespace {
@@ -505,9 +509,59 @@ ft_status launch(ft_ctx *c, const void *fn, int grid, int threads, size_t smem, 
                  cudaStream_t st) {
   if (grid <= 0) return FT_OK;
   void *argv[] = {args};
-  const cudaError_t e = cudaLaunchKernel(fn, dim3(grid), dim3(threads), argv, smem, st);
+  cudaError_t e;
+  if (c->l2_on) {
+    cudaLaunchConfig_t lc = {};
+    lc.gridDim = dim3(grid);
+    lc.blockDim = dim3(threads);
+    lc.dynamicSmemBytes = smem;
+    lc.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeAccessPolicyWindow;
+    attr[0].val.accessPolicyWindow = c->l2_window;
+    lc.attrs = attr;
+    lc.numAttrs = 1;
+    e = cudaLaunchKernelExC(&lc, fn, argv);
+  } else {
+    e = cudaLaunchKernel(fn, dim3(grid), dim3(threads), argv, smem, st);
+  }
   ++c->launches;
   return cuda_status(e);
+}
+
+// The l2_persist window: the address span of the factor matrices (clamped to
+// the device's largest window), marked persisting in L2 for this context's
+// launches.  The context's persisting-L2 limit is raised to the window (or
+// the device maximum) if it is lower; the hit ratio scales the window down
+// to what the limit holds.  Devices without persisting L2 leave it off.
+ft_status setup_l2_window(ft_ctx *c) {
+  const Plan &p = c->p;
+  uintptr_t lo = UINTPTR_MAX, hi = 0;
+  for (int n = 0; n < p.N; ++n) {
+    const uintptr_t a = reinterpret_cast<uintptr_t>(c->A[n]);
+    lo = std::min(lo, a);
+    hi = std::max(hi, a + uintptr_t(p.I[n]) * uintptr_t(p.J[n]) * sizeof(float));
+  }
+  int max_win = 0, max_persist = 0;
+  if (cudaDeviceGetAttribute(&max_win, cudaDevAttrMaxAccessPolicyWindowSize, p.dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&max_persist, cudaDevAttrMaxPersistingL2CacheSize, p.dev) != cudaSuccess)
+    return FT_ERR_CUDA;
+  if (max_win <= 0 || max_persist <= 0 || hi <= lo) return FT_OK;
+  const size_t bytes = std::min<size_t>(hi - lo, size_t(max_win));
+  const size_t want = std::min<size_t>(bytes, size_t(max_persist));
+  size_t cur = 0;
+  if (cudaDeviceGetLimit(&cur, cudaLimitPersistingL2CacheSize) != cudaSuccess) return FT_ERR_CUDA;
+  if (cur < want) {
+    if (cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, want) != cudaSuccess) return FT_ERR_CUDA;
+    cur = want;
+  }
+  c->l2_window.base_ptr = reinterpret_cast<void *>(lo);
+  c->l2_window.num_bytes = bytes;
+  c->l2_window.hitRatio = float(std::min(1.0, double(cur) / double(bytes)));
+  c->l2_window.hitProp = cudaAccessPropertyPersisting;
+  c->l2_window.missProp = cudaAccessPropertyStreaming;
+  c->l2_on = true;
+  return FT_OK;
 }
 
 ft::EpochArgs base_args(ft_ctx *c) {
@@ -738,6 +792,10 @@ ft_status ft_init(ft_ctx **out, int N, const int64_t *I, const int *J, int R, in
   }
   c->vals = vals;
   c->ws = static_cast<char *>(workspace);
+  if (c->p.cfg.l2_persist) {
+    s = setup_l2_window(c);
+    if (s != FT_OK) { delete c; return s; }
+  }
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   if (cudaMemsetAsync(c->ws, 0, c->p.off_partial, st) != cudaSuccess) { delete c; return FT_ERR_CUDA; }
   if (nnz > 0) {

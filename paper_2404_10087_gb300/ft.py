@@ -58,7 +58,7 @@ class ft_config(ctypes.Structure):
                 ("det_batch", ctypes.c_int64), ("blocks_per_sm", ctypes.c_int),
                 ("hot_rows", ctypes.c_int), ("hot_window", ctypes.c_int),
                 ("hot_min_count", ctypes.c_int), ("engine", ctypes.c_int), ("core_scheme", ctypes.c_int),
-                ("reserved", ctypes.c_int * 2)]
+                ("l2_persist", ctypes.c_int), ("reserved", ctypes.c_int * 1)]
 
 
 _lib = None
@@ -145,7 +145,7 @@ def _stream(stream) -> int:
 
 def make_config(precision="fp32", scatter="hogwild", det_batch=4096, blocks_per_sm=0,
                 hot_rows=None, hot_window=None, hot_min_count=None, engine="warp",
-                core_scheme="calc") -> ft_config:
+                core_scheme="calc", l2_persist=False) -> ft_config:
     c = ft_config()
     load().ft_config_default(ctypes.byref(c))
     c.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
@@ -160,6 +160,7 @@ def make_config(precision="fp32", scatter="hogwild", det_batch=4096, blocks_per_
         c.hot_min_count = int(hot_min_count)
     c.engine = ENGINES[engine] if isinstance(engine, str) else int(engine)
     c.core_scheme = CORE_SCHEMES[core_scheme] if isinstance(core_scheme, str) else int(core_scheme)
+    c.l2_persist = int(l2_persist)
     return c
 
 
@@ -280,7 +281,7 @@ class FastTuckerPlus:
 
     def __init__(self, idx, vals, A, B, precision="fp32", scatter="hogwild", det_batch=4096,
                  blocks_per_sm=0, stream=None, hot_rows=None, hot_window=None, hot_min_count=None,
-                 engine="warp", core_scheme="calc"):
+                 engine="warp", core_scheme="calc", l2_persist=False):
         N = len(A)
         if not (len(idx) == len(B) == N):
             raise ValueError("idx, A and B need one entry per mode")
@@ -296,7 +297,7 @@ class FastTuckerPlus:
         self.R = int(B[0].shape[1])
         self.nnz = int(vals.numel())
         self.cfg = make_config(precision, scatter, det_batch, blocks_per_sm, hot_rows, hot_window,
-                               hot_min_count, engine, core_scheme)
+                               hot_min_count, engine, core_scheme, l2_persist)
         ws = ft_workspace_size(self.I, self.J, self.R, self.nnz, self.cfg)
         self.workspace = torch.empty(max(ws, 256), dtype=torch.uint8, device=vals.device)
         self.ctx = ft_init(self.I, self.J, self.R, self.idx, vals, self.A, self.B, self.workspace,

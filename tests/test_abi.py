@@ -81,7 +81,14 @@ def test_core_scheme_configuration():
     lib = ft.load()
     cfg = ft.ft_config()
     lib.ft_config_default(ctypes.byref(cfg))
-    assert cfg.core_scheme == ft.FT_CORE_CALC and list(cfg.reserved) == [0, 0]
+    assert cfg.core_scheme == ft.FT_CORE_CALC and cfg.l2_persist == 0 and list(cfg.reserved) == [0]
     with pytest.raises(ft.FtError) as e:
         ft.ft_workspace_size((10, 10, 10), (16, 16, 16), 16, 100, ft.make_config(core_scheme=5))
+    assert e.value.status == -1
+
+
+def test_l2_persist_configuration():
+    """l2_persist is 0 or 1; other values are refused on the host."""
+    with pytest.raises(ft.FtError) as e:
+        ft.ft_workspace_size((10, 10, 10), (16, 16, 16), 16, 100, ft.make_config(l2_persist=2))
     assert e.value.status == -1

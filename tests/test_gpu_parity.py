@@ -341,6 +341,32 @@ def test_permute_deterministic_mode_and_bad_entries():
     assert e.value.status == -1
 
 
+def test_l2_persist_is_only_a_cache_hint():
+    """With the factor matrices marked persisting in L2 (one allocation, so
+    the window covers only them) the deterministic epoch and the core
+    gradient are bit for bit those of the same context without the hint."""
+    I, J, R, nnz = (90, 80, 70), (16, 16, 16), 16, 3000
+    idx, x, A, B = synth.random_problem(12, I, J, R, nnz)
+    gidx, gx, _, gB = to_dev(idx, x, A, B)
+    flat = torch.cat([a.reshape(-1) for a in A]).to(DEV)
+    views, off = [], 0
+    for a in A:
+        views.append(flat[off:off + a.numel()].view(a.shape))
+        off += a.numel()
+    plain = [a.clone().to(DEV) for a in A]
+    got = []
+    for mats, l2 in ((views, True), (plain, False)):
+        m = ft.FastTuckerPlus(gidx, gx, mats, [b.clone() for b in gB], precision="bf16",
+                              scatter="deterministic", det_batch=256, l2_persist=l2)
+        m.epoch_factors(0.02, 0.01)
+        G = torch.cat([g.reshape(-1) for g in m.core_grad()])
+        m.check()
+        got.append(([t.clone() for t in mats], G.clone()))
+    for a, b in zip(got[0][0], got[1][0]):
+        assert torch.equal(a, b)
+    assert torch.equal(got[0][1], got[1][1])
+
+
 def test_deterministic_mode_is_bitwise_reproducible():
     I, J, R, nnz = (100, 20, 10), (16, 16, 16), 16, 4000
     idx, x, A, B = synth.random_problem(7, I, J, R, nnz)
