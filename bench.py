@@ -337,19 +337,23 @@ def run_ours(args, rank, world, local_rank):
                 dst.copy_(src, non_blocking=True)
             ready[b].record(copy_stream)
 
+    def e2e_run(steps):
+        copy_stream.wait_stream(stream)
+        copy_in(0)
+        for k in range(steps):
+            b = k % 2
+            stream.wait_event(ready[b])
+            m.rebind(bufs[b][0], bufs[b][1])
+            if k + 1 < steps:
+                copy_in(k + 1)
+            step(test=(bufs[b][2], bufs[b][3]))
+            free[b].record(stream)
+
+    e2e_run(args.warmup)          # untimed: first use of the pinned buffers and the second copy
     torch.cuda.synchronize()
     te0, te1 = ev(), ev()
     te0.record(stream)
-    copy_stream.wait_stream(stream)
-    copy_in(0)
-    for k in range(e2e_steps):
-        b = k % 2
-        stream.wait_event(ready[b])
-        m.rebind(bufs[b][0], bufs[b][1])
-        if k + 1 < e2e_steps:
-            copy_in(k + 1)
-        step(test=(bufs[b][2], bufs[b][3]))
-        free[b].record(stream)
+    e2e_run(e2e_steps)
     te1.record(stream)
     torch.cuda.synchronize()
     e2e_ms = te0.elapsed_time(te1) / e2e_steps
@@ -748,9 +752,9 @@ def main():
     ap.add_argument("--engine", choices=["warp", "tcgen05"], default="warp",
                     help="factor-pass kernels: 16-nonzero warp tiles (mma.sync) or 128-nonzero "
                          "warpgroup tiles (tcgen05.mma, TMEM)")
-    ap.add_argument("--l2-persist", type=int, choices=[0, 1], default=1,
+    ap.add_argument("--l2-persist", type=int, choices=[0, 1], default=0,
                     help="mark the factor matrices persisting in L2 for the library's launches "
-                         "(keeps them resident while the end-to-end leg's copies stream in)")
+                         "(measured slower on this workload, so off by default)")
     ap.add_argument("--core-scheme", choices=["calc", "store"], default="calc",
                     help="core phase: rows of C formed per nonzero, or gathered from C = A B "
                          "precomputed once per core phase (Sec. 5.6)")
