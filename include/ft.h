@@ -113,7 +113,8 @@ typedef struct {
    * storage scheme faster on CUDA cores and calculation faster with tensor
    * cores.  Both give the same gradient up to rounding. */
   int core_scheme;
-  /* 1: keep the factor matrices in L2 while other traffic streams through
+  /* (A cache hint with no counterpart in the paper.)
+   * 1: keep the factor matrices in L2 while other traffic streams through
    * it (for example a host-to-device copy of the next epoch's nonzeros that
    * overlaps this epoch): every launch of the context carries an access-policy
    * window over the address span of A^(0..N-1), marked persisting.  ft_init
@@ -187,7 +188,8 @@ ft_status ft_epoch_core(ft_ctx *ctx, float lr_b, float lambda_b, void *stream);
 ft_status ft_permute(ft_ctx *ctx, const int32_t *perm, int32_t *const *idx_out, float *vals_out,
                      void *stream);
 
-/* Point the context at another copy of its training nonzeros: the same nnz,
+/* (A library service with no counterpart in the paper.)  Point the context
+ * at another copy of its training nonzeros: the same nnz,
  * in any order, e.g. a buffer that an asynchronous host-to-device copy filled
  * while the previous epoch ran (double buffering).  The arrays are borrowed
  * from then on; the old ones are no longer read once the calls queued before

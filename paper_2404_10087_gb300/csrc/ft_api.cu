@@ -134,18 +134,31 @@ __global__ void k_store_c(const StoreArgs a) {
   *reinterpret_cast<float4 *>(a.C[n] + row * a.K + r0) = make_float4(acc[0], acc[1], acc[2], acc[3]);
 }
 
+// One warp per element of G: lane l sums the partials of CTAs l, l + 32,
+// ... in order (Neumaier), then the lanes are combined by a fixed xor tree
+// and lane 0 holds the result - the same order on every run.
 __global__ void k_finalize(const FinalizeArgs f) {
-  const int tid = blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t warp = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
   const int KK = f.K * f.K;
-  if (tid >= f.N * KK) return;
-  const int n = tid / KK, j = (tid % KK) / f.K, r = tid % f.K;
+  if (warp >= int64_t(f.N) * KK) return;
+  const int e = int(warp);
+  const int n = e / KK, j = (e % KK) / f.K, r = e % f.K;
   if (j >= f.J[n] || r >= f.R) return;
   float s = 0.f, c = 0.f;
-  for (int q = 0; q < f.nparts; ++q) {
-    const float *pp = f.partial + (size_t(q) * f.N * KK + tid) * 2;
-    ft::neumaier_add(s, c, pp[0]);
-    c += pp[1];
+#pragma unroll 4
+  for (int q = lane; q < f.nparts; q += 32) {
+    const float2 pp = *reinterpret_cast<const float2 *>(f.partial + (size_t(q) * f.N * KK + e) * 2);
+    ft::neumaier_add(s, c, pp.x);
+    c += pp.y;
   }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const float s2 = __shfl_xor_sync(0xffffffffu, s, o), c2 = __shfl_xor_sync(0xffffffffu, c, o);
+    ft::neumaier_add(s, c, s2);
+    c += c2;
+  }
+  if (lane != 0) return;
   const float G = s + c;
   if (f.G_out) f.G_out[f.offG[n] + j * f.R + r] = G;
   if (f.update) {
@@ -950,7 +963,7 @@ static ft_status core_pass(ft_ctx *c, float lr_b, float lambda_b, float *G_out, 
   f.inv_nnz = hi > lo ? float(1.0 / double(hi - lo)) : 0.f;
   f.update = update;
   const int total = p.N * p.K * p.K;
-  return launch(c, reinterpret_cast<const void *>(&k_finalize), (total + 255) / 256, 256, 0, &f, st);
+  return launch(c, reinterpret_cast<const void *>(&k_finalize), (32 * total + 255) / 256, 256, 0, &f, st);
 }
 
 ft_status ft_epoch_core(ft_ctx *c, float lr_b, float lambda_b, void *stream) {
@@ -1117,7 +1130,7 @@ ft_status ft_core_grad_noalloc(int N, const int64_t *I, const int *J, int R, int
   f.update = 0;
   void *argv_fin[] = {&f};
   const int total = N * p.K * p.K;
-  if (cudaLaunchKernel(reinterpret_cast<const void *>(&k_finalize), dim3((total + 255) / 256), dim3(256), argv_fin,
+  if (cudaLaunchKernel(reinterpret_cast<const void *>(&k_finalize), dim3((32 * total + 255) / 256), dim3(256), argv_fin,
                        0, st) != cudaSuccess)
     return FT_ERR_CUDA;
   int h_err = 0;
