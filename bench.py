@@ -498,7 +498,7 @@ def run_sweep(args, local_rank):
     if args.sweep in ("schemes", "all"):
         # Sec. 5.6: the core phase forming the rows of C per nonzero
         # (calculation) or gathering them from C = A B precomputed once per
-        # core phase (storage), on CUDA cores (FP32) and tensor cores
+        # core phase (storage), per precision
         w0, tri, trx, tei, tex, A0, B0 = make_workload(dev, args.nnz, args.workload)
         for prec in ("fp32", "tf32", "bf16"):
             for scheme in ("calc", "store"):
@@ -618,7 +618,7 @@ def learned_step_ab(dev, epochs=20, lr=0.01, lam=0.01):
 
 def time_to_rmse(w, tri, trx, tei, tex, dev, epochs, precision, window=3):
     """Wall time for the mixed-precision run to reach the test RMSE of plain
-    FP32 (CUDA cores), both from the same start.  Hogwild test RMSE wobbles
+    FP32 (the FP32-accurate mode), both from the same start.  Hogwild test RMSE wobbles
     from epoch to epoch, so a run reaches a threshold at the first epoch whose
     mean over the last `window` epochs is at or below it.  Two thresholds:
     'strict' = the FP32 run's final window mean after `epochs` epochs, and

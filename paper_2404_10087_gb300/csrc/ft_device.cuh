@@ -783,13 +783,21 @@ struct GradTile {
                    pack_bf16(Ds[m0 * LD + r0], Ds[(m0 + 1) * LD + r0]),
                    pack_bf16(Ds[m2 * LD + r0], Ds[(m2 + 1) * LD + r0]));
         } else {
+          // FP32: three-pass TF32 (x = hi + lo; lo.hi + hi.lo + hi.hi), the
+          // same fragments as the TF32 path, FP32-accurate
 #pragma unroll
-          for (int i = 0; i < 4; ++i) {
-            const int j = 16 * mt + g + 8 * (i >> 1), r = 8 * u + 2 * t + (i & 1);
-            float s = 0.f;
-#pragma unroll
-            for (int mm = 0; mm < FT_TILE; ++mm) s = fmaf(Es[mm * LD + j], Ds[mm * LD + r], s);
-            acc[i] = s;
+          for (int s = 0; s < 2; ++s) {
+            const int m0 = 8 * s + t, m1 = m0 + 4;
+            uint32_t ah[4], al[4], bh[2], bl[2];
+            Prod<K, MATH_TF32X3>::split(Es[m0 * LD + j0], ah[0], al[0]);
+            Prod<K, MATH_TF32X3>::split(Es[m0 * LD + j0 + 8], ah[1], al[1]);
+            Prod<K, MATH_TF32X3>::split(Es[m1 * LD + j0], ah[2], al[2]);
+            Prod<K, MATH_TF32X3>::split(Es[m1 * LD + j0 + 8], ah[3], al[3]);
+            Prod<K, MATH_TF32X3>::split(Ds[m0 * LD + r0], bh[0], bl[0]);
+            Prod<K, MATH_TF32X3>::split(Ds[m1 * LD + r0], bh[1], bl[1]);
+            mma_tf32(acc, al[0], al[1], al[2], al[3], bh[0], bh[1]);
+            mma_tf32(acc, ah[0], ah[1], ah[2], ah[3], bl[0], bl[1]);
+            mma_tf32(acc, ah[0], ah[1], ah[2], ah[3], bh[0], bh[1]);
           }
         }
 #pragma unroll

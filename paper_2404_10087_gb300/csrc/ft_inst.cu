@@ -21,28 +21,37 @@
 #define FT_CAT_(a, b, c, d) a##_##b##_##c##_##d
 #define FT_CAT(a, b, c, d) FT_CAT_(a, b, c, d)
 
+// Arithmetic of the core-gradient kernels for the precision of this unit:
+// FT_FP32 runs them on FP32-accurate three-pass TF32 tensor-core products
+// (its factor pass stays on the CUDA cores, which measured faster there).
+#if FT_MATH == 0
+#define FT_KMATH ft::MATH_TF32X3
+#else
+#define FT_KMATH FT_MATH
+#endif
+
 namespace {
 template <int N>
 ft::KernelSet make_set() {
   ft::KernelSet s;
   s.factor = reinterpret_cast<const void *>(&ft::k_factor<N, FT_K, FT_MATH, false>);
   s.factor_delta = reinterpret_cast<const void *>(&ft::k_factor<N, FT_K, FT_MATH, true>);
-  s.core = reinterpret_cast<const void *>(&ft::k_core<N, FT_K, FT_MATH>);
+  s.core = reinterpret_cast<const void *>(&ft::k_core<N, FT_K, FT_KMATH>);
   s.factor_smem = ft::FactorSmem<N, FT_K, FT_MATH>::tables();
-  s.core_smem = ft::CoreSmem<N, FT_K, FT_MATH>::bytes();
-  s.core_threads = 32 * ft::CoreSmem<N, FT_K, FT_MATH>::WARPS;
+  s.core_smem = ft::CoreSmem<N, FT_K, FT_KMATH>::bytes();
+  s.core_threads = 32 * ft::CoreSmem<N, FT_K, FT_KMATH>::WARPS;
   s.batch_factor = reinterpret_cast<const void *>(&ft::k_batch_factor<N, FT_K, FT_MATH>);
-  s.batch_core = reinterpret_cast<const void *>(&ft::k_batch_core<N, FT_K, FT_MATH>);
-  s.batch_core_smem = ft::CoreSmem<N, FT_K, FT_MATH>::bytes();
-  s.batch_core_threads = 32 * ft::CoreSmem<N, FT_K, FT_MATH>::WARPS;
+  s.batch_core = reinterpret_cast<const void *>(&ft::k_batch_core<N, FT_K, FT_KMATH>);
+  s.batch_core_smem = ft::CoreSmem<N, FT_K, FT_KMATH>::bytes();
+  s.batch_core_threads = 32 * ft::CoreSmem<N, FT_K, FT_KMATH>::WARPS;
 #if FT_MATH == 2
   s.core_store = reinterpret_cast<const void *>(&ft::k_core_coop<N, FT_K, true>);
   s.core_store_smem = ft::CoopSmem<N, FT_K>::bytes();
   s.core_store_threads = 32 * ft::CoopSmem<N, FT_K>::WARPS;
 #else
-  s.core_store = reinterpret_cast<const void *>(&ft::k_core<N, FT_K, FT_MATH, true>);
-  s.core_store_smem = ft::CoreSmem<N, FT_K, FT_MATH>::bytes();
-  s.core_store_threads = 32 * ft::CoreSmem<N, FT_K, FT_MATH>::WARPS;
+  s.core_store = reinterpret_cast<const void *>(&ft::k_core<N, FT_K, FT_KMATH, true>);
+  s.core_store_smem = ft::CoreSmem<N, FT_K, FT_KMATH>::bytes();
+  s.core_store_threads = 32 * ft::CoreSmem<N, FT_K, FT_KMATH>::WARPS;
 #endif
 #if FT_MATH == 2
   // BF16: the CTA-cooperative core pass

@@ -92,3 +92,16 @@ def test_l2_persist_configuration():
     with pytest.raises(ft.FtError) as e:
         ft.ft_workspace_size((10, 10, 10), (16, 16, 16), 16, 100, ft.make_config(l2_persist=2))
     assert e.value.status == -1
+
+
+def test_context_calls_refuse_a_null_context():
+    """The per-context calls return FT_ERR_ARG for a null context before any
+    device work."""
+    lib = ft.load()
+    assert lib.ft_epoch_factors(None, 0.1, 0.1, None, None) == -1
+    assert lib.ft_epoch_core(None, 0.1, 0.1, None) == -1
+    assert lib.ft_epoch_core_sgd(None, 0.1, 0.1, 100, None) == -1
+    assert lib.ft_permute(None, None, None, None, None) == -1
+    assert lib.ft_rebind(None, None, None, None) == -1
+    assert lib.ft_core_grad(None, None, None) == -1
+    assert lib.ft_check(None, None) == -1
