@@ -248,6 +248,11 @@ struct ft_batch {
   Layout L;
   char *ws = nullptr;
   cudaStream_t capture = nullptr;
+  // per-class streams and join events: each class's factor and core passes
+  // form one branch of the captured graph, all branches joining at finalize
+  std::vector<cudaStream_t> branch;
+  std::vector<cudaEvent_t> joined;
+  cudaEvent_t forked = nullptr;
   cudaGraphExec_t exec = nullptr;
   int64_t launches = 0;
   int64_t graph_kernels = 0;
@@ -336,26 +341,41 @@ cudaError_t launch_core(ft_batch *b, const ClassInfo &c, cudaStream_t st) {
                           c.ks.batch_core_smem, st);
 }
 
-// Capture factor passes, core passes and the finalize into one graph.
+// Capture factor passes, core passes and the finalize into one graph: the
+// classes touch disjoint tensors, so each class's factor pass -> core pass
+// is its own branch (concurrent with the other classes), and the finalize
+// over every tensor waits for all branches.
 ft_status capture(ft_batch *b) {
   if (b->exec) {
     cudaGraphExecDestroy(b->exec);
     b->exec = nullptr;
   }
   cudaStream_t st = b->capture;
+  const size_t nc = b->classes.size();
+  while (b->branch.size() < nc) {
+    cudaStream_t s2 = nullptr;
+    cudaEvent_t e2 = nullptr;
+    if (cudaStreamCreateWithFlags(&s2, cudaStreamNonBlocking) != cudaSuccess) return FT_ERR_CUDA;
+    b->branch.push_back(s2);
+    if (cudaEventCreateWithFlags(&e2, cudaEventDisableTiming) != cudaSuccess) return FT_ERR_CUDA;
+    b->joined.push_back(e2);
+  }
+  if (!b->forked && cudaEventCreateWithFlags(&b->forked, cudaEventDisableTiming) != cudaSuccess) return FT_ERR_CUDA;
   if (cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return FT_ERR_CUDA;
-  bool ok = true;
+  bool ok = cudaEventRecord(b->forked, st) == cudaSuccess;
   int64_t kernels = 0;
-  for (const ClassInfo &c : b->classes) {
+  for (size_t k = 0; k < nc; ++k) {
+    const ClassInfo &c = b->classes[k];
+    cudaStream_t bs = b->branch[k];
+    ok = ok && cudaStreamWaitEvent(bs, b->forked, 0) == cudaSuccess;
     ft::BatchArgs a = class_args(b, c);
     void *argv[] = {&a};
     ok = ok && cudaLaunchKernel(c.ks.batch_factor, dim3(class_grid(b, c, false)), dim3(256), argv,
-                                c.ks.factor_smem, st) == cudaSuccess;
-    ++kernels;
-  }
-  for (const ClassInfo &c : b->classes) {
-    ok = ok && launch_core(b, c, st) == cudaSuccess;
-    ++kernels;
+                                c.ks.factor_smem, bs) == cudaSuccess;
+    ok = ok && launch_core(b, c, bs) == cudaSuccess;
+    ok = ok && cudaEventRecord(b->joined[k], bs) == cudaSuccess;
+    ok = ok && cudaStreamWaitEvent(st, b->joined[k], 0) == cudaSuccess;
+    kernels += 2;
   }
   int64_t total = 0;
   for (const TensorInfo &ti : b->tensors) total += int64_t(ti.N) * ti.K * ti.K;
@@ -617,6 +637,9 @@ int64_t ft_batch_launch_count(const ft_batch *b) { return b ? b->launches : 0; }
 void ft_batch_destroy(ft_batch *b) {
   if (!b) return;
   if (b->exec) cudaGraphExecDestroy(b->exec);
+  for (cudaStream_t s2 : b->branch) cudaStreamDestroy(s2);
+  for (cudaEvent_t e2 : b->joined) cudaEventDestroy(e2);
+  if (b->forked) cudaEventDestroy(b->forked);
   if (b->capture) cudaStreamDestroy(b->capture);
   delete b;
 }
