@@ -206,19 +206,29 @@ struct RemapArgs {
   int64_t I[FT_MAXN];
   int N;
   int64_t nnz;
+  int vec;            // every idx[n] and out[n] 16-byte aligned: 4 coordinates per access
 };
+
+__device__ __forceinline__ int32_t remap_one(const RemapArgs &a, int n, int32_t v) {
+  const int32_t sl = (v >= 0 && int64_t(v) < a.I[n]) ? __ldg(a.slot_of[n] + v) : -1;
+  return sl >= 0 ? -(sl + 1) : v;
+}
 
 // Coordinates of the Hogwild pass: a cached row becomes -(slot + 1).  A
 // coordinate outside [0, I_n) is passed through unchanged (the epoch kernels
 // mask it and latch FT_ERR_INDEX).
 __global__ void k_remap(const RemapArgs a) {
-  for (int64_t m = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; m < a.nnz;
-       m += int64_t(gridDim.x) * blockDim.x)
+  const int64_t tid = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+  const int64_t n4 = a.vec ? a.nnz / 4 : 0;
+  for (int64_t q = tid; q < n4; q += stride)
     for (int n = 0; n < a.N; ++n) {
-      const int32_t v = a.idx[n][m];
-      const int32_t sl = (v >= 0 && int64_t(v) < a.I[n]) ? a.slot_of[n][v] : -1;
-      a.out[n][m] = sl >= 0 ? -(sl + 1) : v;
+      const int4 v = __ldcs(reinterpret_cast<const int4 *>(a.idx[n]) + q);
+      __stcs(reinterpret_cast<int4 *>(a.out[n]) + q,
+             make_int4(remap_one(a, n, v.x), remap_one(a, n, v.y), remap_one(a, n, v.z), remap_one(a, n, v.w)));
     }
+  for (int64_t m = 4 * n4 + tid; m < a.nnz; m += stride)
+    for (int n = 0; n < a.N; ++n) a.out[n][m] = remap_one(a, n, a.idx[n][m]);
 }
 
 // Reordered copy of the nonzeros: out[n][m] = idx[n][perm[m]],
@@ -668,8 +678,11 @@ ft_status remap_hot(ft_ctx *c, cudaStream_t st) {
   }
   ra.N = p.N;
   ra.nnz = p.nnz;
-  const int grid = int(std::min<int64_t>((p.nnz + 255) / 256, int64_t(p.num_sms) * 8));
-  return launch(c, reinterpret_cast<const void *>(&k_remap), grid, 256, 0, &ra, st);
+  ra.vec = 1;
+  for (int n = 0; n < p.N; ++n)
+    if ((reinterpret_cast<uintptr_t>(ra.idx[n]) | reinterpret_cast<uintptr_t>(ra.out[n])) % 16 != 0) ra.vec = 0;
+  const int grid = int(std::min<int64_t>((p.nnz + 1023) / 1024, int64_t(p.num_sms) * 8));
+  return launch(c, reinterpret_cast<const void *>(&k_remap), std::max(grid, 1), 256, 0, &ra, st);
 }
 
 // Hot-row cache of the Hogwild pass: count the nonzeros of every row, keep

@@ -902,20 +902,19 @@ __global__ void __launch_bounds__(256) k_core(const EpochArgs p) {
 }
 
 // ------------------------------------ core phase, CTA-cooperative (BF16)
-// The core-gradient pass (Algorithm 5) for BF16 at padded rank K = 32, and at
-// K = 16 for orders whose per-lane state does not fit k_core_bf16p.  Since
-// E^(n) = (xhat - x) * A_Psi^(n) (row-wise scaling),
+// The core-gradient pass (Algorithm 5) for BF16, every order and padded rank.
+// Since E^(n) = (xhat - x) * A_Psi^(n) (row-wise scaling),
 //   G^(n) = E^(n)T D^(n) = A_Psi^(n)T ((xhat - x) * D^(n)),
 // so the residual is folded into D and the contraction runs over the raw rows.
-// A CTA tile is 8 warp tiles (128 nonzeros):
+// A CTA tile is WARPS warp tiles (WARPS x 16 nonzeros):
 //   phase 1  each warp gathers its 16 nonzeros' rows, forms C^(n) = A_Psi B
 //            (Prod), xhat and D^(n), and stores A_Psi^(n) and
 //            (xhat - x) * D^(n) as BF16 rows in shared memory;
 //   phase 2  the N (K/16)^2 output blocks of 16 x 16 (mode n, rows j of
 //            G^(n), columns r) are dealt to the warps; each contracts its
-//            blocks over the 128 nonzeros (ldmatrix.trans operands, 8 k-steps
-//            of mma.sync m16n8k16, FP32 accumulation) and adds the CTA tile's
-//            block into Neumaier (sum, compensation) registers.
+//            blocks over the CTA tile's nonzeros (ldmatrix.trans operands,
+//            WARPS k-steps of mma.sync m16n8k16, FP32 accumulation) and adds
+//            the CTA tile's block into Neumaier (sum, compensation) registers.
 // Every output element has exactly one owning warp, so the CTA partial needs
 // no combine; fixed grid and tile order make the pass reproducible bit for bit.
 __device__ __forceinline__ void ldsm_x4(uint32_t addr, uint32_t &r0, uint32_t &r1, uint32_t &r2, uint32_t &r3) {
@@ -972,7 +971,9 @@ struct CoopProd {
 
 template <int N, int K>
 struct CoopSmem {
-  static constexpr int WARPS = 8;
+  // 4-warp CTAs (64-nonzero tiles, six per SM) at K = 16, N <= 3: shorter
+  // barriers, measured 1% faster than 8-warp CTAs; 8 warps elsewhere
+  static constexpr int WARPS = (K == 16 && N <= 3) ? 4 : 8;
   static constexpr int ROWS = WARPS * FT_TILE;              // nonzeros per CTA tile
   static constexpr int LDB = 2 * K + 16;                    // bytes per staged row (conflict-free ldmatrix)
   static constexpr int BUF = ROWS * LDB;                    // bytes of one [ROWS][K] bf16 buffer
@@ -984,10 +985,10 @@ struct CoopSmem {
   // the gathered registers.  It frees the registers that let two CTAs share
   // an SM at (K, N) = (16, 6) and (32, 3); elsewhere it measured 3-4% slower.
   static constexpr bool A_SMEM = (K == 16 && N == 6) || (K == 32 && N == 3);
-  // CTAs per SM (the launch bound caps the registers to fit them): three at
-  // K = 16, N <= 3 (75 registers, no spills), two up to N = 6 and at K = 32,
-  // N = 3, else one
-  static constexpr int MINB = (K == 16 && N <= 3) ? 3 : ((K == 16 && N <= 6) || (K == 32 && N == 3)) ? 2 : 1;
+  // CTAs per SM (the launch bound caps the registers to fit them): six
+  // 4-warp CTAs at K = 16, N <= 3 (79 registers, no spills), two up to N = 6
+  // and at K = 32, N = 3, else one
+  static constexpr int MINB = (K == 16 && N <= 3) ? 6 : ((K == 16 && N <= 6) || (K == 32 && N == 3)) ? 2 : 1;
   static constexpr size_t bytes() { return size_t(TAB) + size_t(2) * N * BUF; }
 };
 
@@ -1007,7 +1008,7 @@ __device__ __forceinline__ void coop_store(unsigned char *dst, const uint32_t (&
 
 // STORE: the storage scheme (rows of C read from p.cst, Sec. 5.6).
 template <int N, int K, bool STORE = false>
-__global__ void __launch_bounds__(256, CoopSmem<N, K>::MINB) k_core_coop(const EpochArgs p) {
+__global__ void __launch_bounds__(32 * CoopSmem<N, K>::WARPS, CoopSmem<N, K>::MINB) k_core_coop(const EpochArgs p) {
   using L = CoopSmem<N, K>;
   static_assert(CoopProd<K>::WORDS == Prod<K, MATH_BF16>::WORDS, "one table size for both C paths");
   constexpr int CPL = K / 4;
@@ -1086,7 +1087,7 @@ __global__ void __launch_bounds__(256, CoopSmem<N, K>::MINB) k_core_coop(const E
       }
     }
     __syncthreads();
-    // phase 2: this warp's output blocks over the CTA tile's 128 nonzeros
+    // phase 2: this warp's output blocks over the CTA tile's nonzeros
 #pragma unroll
     for (int u = 0; u < L::UPW; ++u) {
       const int unit = w + L::WARPS * u;

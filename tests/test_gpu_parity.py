@@ -228,11 +228,13 @@ def test_row_step_scale_deterministic():
 @pytest.mark.parametrize("cache", [dict(hot_rows=0), dict(hot_min_count=1), dict(hot_min_count=1, hot_window=1)],
                          ids=["no_cache", "all_rows_cacheable", "window_1"])
 @pytest.mark.parametrize("precision", ["fp32", "tf32", "bf16"])
-def test_hogwild_without_collisions_is_exact(precision, cache):
+@pytest.mark.parametrize("nnz", [16 * 50 + 3, 16 * 50], ids=["ragged", "multiple_of_4"])
+def test_hogwild_without_collisions_is_exact(precision, cache, nnz):
     """When no two nonzeros share a row in any mode, the Hogwild pass has no
     races and equals the sequential epoch - with or without the shared-memory
-    cache of hot rows (hot_min_count = 1 lets every row be cached)."""
-    nnz = 16 * 50 + 3
+    cache of hot rows (hot_min_count = 1 lets every row be cached; a nonzero
+    count that is a multiple of 4 takes the vector path of the coordinate
+    remap)."""
     I, J, R = (nnz + 5, nnz + 9, nnz), (16, 16, 16), 16
     g = torch.Generator().manual_seed(6)
     idx = torch.stack([torch.randperm(In, generator=g)[:nnz] for In in I]).to(torch.int32)
