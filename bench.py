@@ -275,7 +275,7 @@ def run_ours(args, rank, world, local_rank):
 
     ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
 
-    def step(record=None, test=(tei, tex)):
+    def step(record=None, test=(tei, tex), after_core=None):
         e0, e1, e2, e3 = (ev(), ev(), ev(), ev()) if record is not None else (None,) * 4
         if record is not None:
             e0.record(stream)
@@ -285,6 +285,8 @@ def run_ours(args, rank, world, local_rank):
         m.epoch_core(LR_B, LAM)
         if record is not None:
             e2.record(stream)
+        if after_core is not None:
+            after_core()
         r = m.rmse(*test)  # synchronises: the step's result reaches the host
         if record is not None:
             e3.record(stream)
@@ -318,8 +320,9 @@ def run_ours(args, rank, world, local_rank):
     # end to end through the C ABI with host buffers: every step copies its
     # inputs (the training and the test COO) from pinned host memory and
     # reads the RMSE back.  Two device copies of the inputs alternate: while
-    # step k trains on one (after ft_rebind points the context at it), a
-    # second stream copies step k+1's inputs into the other.
+    # step k trains on one, a second stream copies step k+1's inputs into the
+    # other and, once step k's passes are enqueued, points the context at it
+    # (ft_rebind rebuilds the hot-row coordinates on that stream).
     host_in = [t.cpu().pin_memory() for t in list(tri) + [trx] + list(tei) + [tex]]
     h2d = sum(t.numel() * t.element_size() for t in host_in)
     e2e_steps = max(1, min(args.steps, 10))
@@ -335,18 +338,24 @@ def run_ours(args, rank, world, local_rank):
             copy_stream.wait_event(free[b])        # the step that last read buffer b is done
             for dst, src in zip(dev_in[b], host_in):
                 dst.copy_(src, non_blocking=True)
-            ready[b].record(copy_stream)
+
+    def rebind_in(k):
+        b = k % 2
+        m.rebind(bufs[b][0], bufs[b][1], stream=copy_stream)   # after the copy, same stream
+        ready[b].record(copy_stream)
 
     def e2e_run(steps):
         copy_stream.wait_stream(stream)
         copy_in(0)
+        rebind_in(0)
         for k in range(steps):
             b = k % 2
             stream.wait_event(ready[b])
-            m.rebind(bufs[b][0], bufs[b][1])
+            nxt = None
             if k + 1 < steps:
                 copy_in(k + 1)
-            step(test=(bufs[b][2], bufs[b][3]))
+                nxt = (lambda kk=k + 1: rebind_in(kk))
+            step(test=(bufs[b][2], bufs[b][3]), after_core=nxt)
             free[b].record(stream)
 
     e2e_run(args.warmup)          # untimed: first use of the pinned buffers and the second copy

@@ -198,8 +198,12 @@ ft_status ft_permute(ft_ctx *ctx, const int32_t *perm, int32_t *const *idx_out, 
  * while the previous epoch ran (double buffering).  The arrays are borrowed
  * from then on; the old ones are no longer read once the calls queued before
  * this one have run.  The hot rows chosen at ft_init are kept and their
- * coordinates are rebuilt on the device; in FT_DETERMINISTIC mode the row
- * grouping is rebuilt on the host (synchronises); otherwise asynchronous.
+ * coordinates are rebuilt on the device into the idle one of two copies in
+ * the workspace, on `stream`: the passes enqueued since the previous
+ * ft_rebind (on any stream) read the other copy, so the rebuild may overlap
+ * them on a second stream; passes enqueued later must be ordered after
+ * `stream` (the same stream, or an event).  In FT_DETERMINISTIC mode the row grouping is rebuilt on the
+ * host (synchronises); otherwise asynchronous.
  * The new coordinates and values are not validated up front: the epoch
  * kernels mask a coordinate outside [0, I_n) and latch FT_ERR_INDEX, and a
  * non-finite value shows as a latched FT_ERR_NONFINITE (both reported by the

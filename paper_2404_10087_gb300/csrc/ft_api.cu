@@ -342,6 +342,7 @@ struct Plan {
   size_t off_err = 0, off_out = 0, off_partial = 0, off_errpart = 0, off_delta = 0;
   size_t off_order = 0, off_segptr = 0, off_segrow = 0;
   size_t off_remap = 0, off_hot = 0, off_counts = 0, off_stats = 0, off_cst = 0, total = 0;
+  size_t remap_bytes = 0;            // one of the two remapped coordinate copies
   int64_t rows = 0, grows = 0;      // sum I_n and sum I_n J_n
   // core-gradient kernel of the configured scheme (calculation or storage)
   const void *core_fn = nullptr;
@@ -474,7 +475,9 @@ ft_status make_plan(int N, const int64_t *I, const int *J, int R, int64_t nnz, c
   if (p->hot_cap > 0) {
     int64_t sumI = 0;
     for (int n = 0; n < N; ++n) sumI += I[n];
-    p->off_remap = off;  off += align_up(sizeof(int32_t) * size_t(N) * nnz);
+    // two copies: ft_rebind fills the idle one while epochs still read the other
+    p->remap_bytes = align_up(sizeof(int32_t) * size_t(N) * nnz);
+    p->off_remap = off;  off += 2 * p->remap_bytes;
     p->off_hot = off;    off += align_up(sizeof(int32_t) * size_t(p->hot_cap));
     p->off_counts = off; off += align_up(sizeof(int32_t) * size_t(sumI));
   }
@@ -514,6 +517,7 @@ struct ft_ctx {
   std::vector<int64_t> seg_lo[FT_MAXN];  // per mode: first segment of each batch (+ end)
   int hot_base[FT_MAXN + 1] = {0};       // cache slots of mode n: [base[n], base[n+1])
   bool hot_active = false;
+  int remap_cur = 0;                     // which remapped copy the Hogwild pass reads
   int64_t launches = 0;
   // l2_persist: the access-policy window over the factor matrices that every
   // launch of this context carries
@@ -663,15 +667,16 @@ ft_status build_segments(ft_ctx *c, cudaStream_t st) {
 }
 
 // The Hogwild pass's copy of the coordinates with cached rows remapped to
-// -(slot + 1); the slot of each row (or -1) sits in the counts region.
-ft_status remap_hot(ft_ctx *c, cudaStream_t st) {
+// -(slot + 1), written into remapped copy `target` (0 or 1); the slot of each
+// row (or -1) sits in the counts region.
+ft_status remap_hot(ft_ctx *c, cudaStream_t st, int target) {
   const Plan &p = c->p;
   RemapArgs ra;
   memset(&ra, 0, sizeof(ra));
   int64_t off = 0;
   for (int n = 0; n < p.N; ++n) {
     ra.idx[n] = c->idx[n];
-    ra.out[n] = ws_ptr<int32_t>(c, p.off_remap) + size_t(n) * p.nnz;
+    ra.out[n] = ws_ptr<int32_t>(c, p.off_remap + size_t(target) * p.remap_bytes) + size_t(n) * p.nnz;
     ra.slot_of[n] = ws_ptr<int32_t>(c, p.off_counts) + off;
     ra.I[n] = p.I[n];
     off += p.I[n];
@@ -751,7 +756,8 @@ ft_status build_hot_cache(ft_ctx *c, cudaStream_t st) {
       cudaMemcpyAsync(d_counts, slot_of.data(), sizeof(int32_t) * sumI, cudaMemcpyHostToDevice, st) !=
           cudaSuccess)
     return FT_ERR_CUDA;
-  s = remap_hot(c, st);
+  c->remap_cur = 0;
+  s = remap_hot(c, st, 0);
   if (s != FT_OK) return s;
   return cudaStreamSynchronize(st) == cudaSuccess ? FT_OK : FT_ERR_CUDA;
 }
@@ -871,7 +877,8 @@ ft_status ft_epoch_factors(ft_ctx *c, float lr_a, float lambda_a, const float *c
     for (int n = 0; n < p.N; ++n) a.scale[n] = row_step_scale[n];
   if (p.cfg.scatter == FT_HOGWILD) {
     if (c->hot_active) {
-      for (int n = 0; n < p.N; ++n) a.idx[n] = ws_ptr<int32_t>(c, p.off_remap) + size_t(n) * p.nnz;
+      for (int n = 0; n < p.N; ++n)
+        a.idx[n] = ws_ptr<int32_t>(c, p.off_remap + size_t(c->remap_cur) * p.remap_bytes) + size_t(n) * p.nnz;
       for (int n = 0; n <= p.N; ++n) a.hot_base[n] = c->hot_base[n];
       a.hot_rows = ws_ptr<int32_t>(c, p.off_hot);
       a.hot_cap = p.hot_cap;
@@ -1013,8 +1020,9 @@ ft_status ft_permute(ft_ctx *c, const int32_t *perm, int32_t *const *idx_out, fl
   for (int n = 0; n < p.N; ++n) c->idx[n] = idx_out[n];
   c->vals = vals_out;
   if (c->hot_active) {
-    s = remap_hot(c, st);
+    s = remap_hot(c, st, 1 - c->remap_cur);
     if (s != FT_OK) return s;
+    c->remap_cur = 1 - c->remap_cur;
   }
   if (p.cfg.scatter == FT_DETERMINISTIC) return build_segments(c, st);
   return FT_OK;
@@ -1031,8 +1039,11 @@ ft_status ft_rebind(ft_ctx *c, const int32_t *const *idx, const float *vals, voi
   for (int n = 0; n < p.N; ++n) c->idx[n] = idx[n];
   c->vals = vals;
   if (c->hot_active) {
-    const ft_status s = remap_hot(c, st);
+    // the idle remapped copy: passes enqueued before this call keep reading the
+    // other one, so the rebuild may run on another stream while they finish
+    const ft_status s = remap_hot(c, st, 1 - c->remap_cur);
     if (s != FT_OK) return s;
+    c->remap_cur = 1 - c->remap_cur;
   }
   if (p.cfg.scatter == FT_DETERMINISTIC) return build_segments(c, st);
   return FT_OK;

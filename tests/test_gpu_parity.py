@@ -309,6 +309,21 @@ def test_rebind_to_another_copy():
     torch.cuda.synchronize()
     for a, b in zip(gA, fresh):
         assert torch.equal(a, b)
+    # a rebind enqueued on a second stream while this context's epoch is still
+    # queued on the current one (the rebuild goes to the idle remapped copy)
+    cidx2, cx2 = [t.clone() for t in cidx], cx.clone()
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    m.epoch_factors(0.03, 0.02)
+    m.rebind(cidx2, cx2, stream=side)
+    torch.cuda.current_stream().wait_stream(side)
+    m.epoch_factors(0.03, 0.02)
+    m.check()
+    m2.epoch_factors(0.03, 0.02)
+    m2.epoch_factors(0.03, 0.02)
+    torch.cuda.synchronize()
+    for a, b in zip(gA, fresh):
+        assert torch.equal(a, b)
     bad = [t.clone() for t in cidx]
     bad[1][3] = I[1]
     m.rebind(bad, cx)
