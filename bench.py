@@ -325,7 +325,7 @@ def run_ours(args, rank, world, local_rank):
     # (ft_rebind rebuilds the hot-row coordinates on that stream).
     host_in = [t.cpu().pin_memory() for t in list(tri) + [trx] + list(tei) + [tex]]
     h2d = sum(t.numel() * t.element_size() for t in host_in)
-    e2e_steps = max(1, min(args.steps, 10))
+    e2e_steps = max(1, args.steps)           # the same K steps as the device-resident leg
     dev_in = [list(tri) + [trx] + list(tei) + [tex], [torch.empty_like(t, device=dev) for t in host_in]]
     bufs = [(d[:N], d[N], d[N + 1:2 * N + 1], d[2 * N + 1]) for d in dev_in]
     copy_stream = torch.cuda.Stream(dev)
