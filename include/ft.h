@@ -227,6 +227,23 @@ ft_status ft_epoch_core_sgd(ft_ctx *ctx, float lr_b, float lambda_b, int64_t set
  * n = 0..N-1, each J_n x R row-major, concatenated. */
 ft_status ft_core_grad(ft_ctx *ctx, float *G_out, void *stream);
 
+/* The core step of Algorithm 5 from a gradient that the caller supplies:
+ *   B^(n) <- B^(n) - lr_b (G^(n) / nnz_total + lambda_b B^(n))
+ * for every entry, in the context's B (in place).  With ft_core_grad this
+ * splits ft_epoch_core into its two halves, so that the gradient can be
+ * summed across processes in between: each process holds a context over its
+ * own shard of Omega (Algorithm 5 sums G over all of Omega, so the shards'
+ * gradients add), the processes all-reduce their G_out, and each applies the
+ * sum with nnz_total = |Omega| (the sum of the shards' nnz), which leaves
+ * identical B on every process.  ft_core_grad followed by ft_core_apply with
+ * nnz_total = the context's nnz equals ft_epoch_core bit for bit.
+ *   G         device, sum_n J_n * R floats in the layout of ft_core_grad's
+ *             G_out (mode by mode, each J_n x R row-major); used as given
+ *   nnz_total >= 0 (0 applies only the decay term, as an empty Omega would)
+ * FT_ERR_ARG for a null pointer, a negative nnz_total or a non-finite step. */
+ft_status ft_core_apply(ft_ctx *ctx, const float *G, int64_t nnz_total, float lr_b,
+                        float lambda_b, void *stream);
+
 /* The core gradient of ft_core_grad without a context and without any
  * allocation, for callers that cannot call cudaMalloc: for example code whose
  * device memory is owned by another allocator (a framework or service that

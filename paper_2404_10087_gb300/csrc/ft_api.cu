@@ -1065,6 +1065,50 @@ ft_status ft_core_grad(ft_ctx *c, float *G_out, void *stream) {
   return core_pass(c, 0.f, 0.f, G_out, 0, static_cast<cudaStream_t>(stream));
 }
 
+struct CoreApplyArgs {
+  const float *G;        // sum_n J_n R entries, the layout of ft_core_grad
+  float *B[FT_MAXN];
+  int offG[FT_MAXN + 1];  // first entry of mode n's block; offG[N] = total
+  int N;
+  float lr, lam, inv_nnz;
+};
+
+// The step of Algorithm 5 from a gradient summed elsewhere (for example over
+// the shards of Omega held by several processes): one thread per entry,
+// B <- B - lr (G inv_nnz + lam B), the arithmetic of k_finalize's update.
+__global__ void k_core_apply(const CoreApplyArgs a) {
+  const int e = int(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (e >= a.offG[a.N]) return;
+  int n = 0;
+  while (n + 1 < a.N && e >= a.offG[n + 1]) ++n;
+  float *b = a.B[n] + (e - a.offG[n]);
+  const float bv = *b;
+  *b = bv - a.lr * fmaf(__ldg(a.G + e), a.inv_nnz, a.lam * bv);
+}
+
+ft_status ft_core_apply(ft_ctx *c, const float *G, int64_t nnz_total, float lr_b, float lambda_b,
+                        void *stream) {
+  if (!c || !G || nnz_total < 0) return FT_ERR_ARG;
+  if (!std::isfinite(lr_b) || !std::isfinite(lambda_b)) return FT_ERR_ARG;
+  const Plan &p = c->p;
+  CoreApplyArgs a;
+  memset(&a, 0, sizeof(a));
+  a.G = G;
+  a.N = p.N;
+  int off = 0;
+  for (int n = 0; n < p.N; ++n) {
+    a.B[n] = c->B[n];
+    a.offG[n] = off;
+    off += p.J[n] * p.R;
+  }
+  a.offG[p.N] = off;
+  a.lr = lr_b;
+  a.lam = lambda_b;
+  a.inv_nnz = nnz_total > 0 ? float(1.0 / double(nnz_total)) : 0.f;
+  return launch(c, reinterpret_cast<const void *>(&k_core_apply), (off + 255) / 256, 256, 0, &a,
+                static_cast<cudaStream_t>(stream));
+}
+
 // ---------------------------------------------- core gradient, no allocation
 // Scratch of ft_core_grad_noalloc: a 256-byte error word followed by the
 // per-CTA (sum, compensation) partials of the core-gradient kernel.  It is a

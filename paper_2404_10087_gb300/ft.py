@@ -33,7 +33,8 @@ STATUS = {0: "FT_OK", -1: "FT_ERR_ARG", -2: "FT_ERR_INDEX", -3: "FT_ERR_SHAPE", 
 
 # Every symbol the header declares (checked by the tests against the library).
 EXPORTS = ["ft_config_default", "ft_workspace_size", "ft_init", "ft_epoch_factors",
-           "ft_epoch_core", "ft_epoch_core_sgd", "ft_permute", "ft_rebind", "ft_core_grad", "ft_predict", "ft_rmse", "ft_check",
+           "ft_epoch_core", "ft_epoch_core_sgd", "ft_permute", "ft_rebind", "ft_core_grad",
+           "ft_core_apply", "ft_predict", "ft_rmse", "ft_check",
            "ft_launch_count", "ft_destroy", "ft_status_str", "ft_core_grad_noalloc",
            "ft_batch_workspace_size", "ft_batch_init", "ft_batch_tune", "ft_batch_epoch",
            "ft_batch_rmse", "ft_batch_num_classes", "ft_batch_class_info", "ft_batch_launch_count",
@@ -99,6 +100,7 @@ def _declare(lib):
         "ft_permute": (INT, [_P, _P, _P, _P, _P]),
         "ft_rebind": (INT, [_P, _P, _P, _P]),
         "ft_core_grad": (INT, [_P, _P, _P]),
+        "ft_core_apply": (INT, [_P, _P, I64, FLT, FLT, _P]),
         "ft_predict": (INT, [_P, I64, _P, _P, _P]),
         "ft_rmse": (INT, [_P, I64, _P, _P, _P, _P]),
         "ft_check": (INT, [_P, _P]),
@@ -223,6 +225,11 @@ def ft_core_grad(ctx, G_out, stream=None):
     _check(load().ft_core_grad(ctx, G_out.data_ptr(), _stream(stream)), "ft_core_grad")
 
 
+def ft_core_apply(ctx, G, nnz_total, lr_b, lambda_b, stream=None):
+    _check(load().ft_core_apply(ctx, G.data_ptr(), int(nnz_total), float(lr_b), float(lambda_b),
+                                _stream(stream)), "ft_core_apply")
+
+
 def ft_core_grad_noalloc(idx, vals, A, B, G_out, precision="fp32", stream=None):
     """Core gradient without a context or workspace (the library's static
     scratch is used; see include/ft.h).  idx, A, B: lists of device tensors;
@@ -343,6 +350,16 @@ class FastTuckerPlus:
             out.append(G[off:off + j * self.R].view(j, self.R))
             off += j * self.R
         return out
+
+    def core_apply(self, G, nnz_total, lr, lam, stream=None):
+        """B <- B - lr (G / nnz_total + lam B), G flat in the layout of
+        ft_core_grad (or a list of J_n x R tensors, concatenated here)."""
+        if isinstance(G, (list, tuple)):
+            G = torch.cat([g.reshape(-1) for g in G])
+        if not G.is_cuda or G.dtype != torch.float32 or not G.is_contiguous() \
+                or G.numel() != sum(j * self.R for j in self.J):
+            raise ValueError("G must be a contiguous float32 CUDA tensor of sum_n J_n R entries")
+        ft_core_apply(self.ctx, G, nnz_total, lr, lam, stream)
 
     def predict(self, idx, stream=None):
         out = torch.empty(int(idx[0].numel()), dtype=torch.float32, device=self.vals.device)
