@@ -342,6 +342,7 @@ struct Plan {
   size_t off_err = 0, off_out = 0, off_partial = 0, off_errpart = 0, off_delta = 0;
   size_t off_order = 0, off_segptr = 0, off_segrow = 0;
   size_t off_remap = 0, off_hot = 0, off_counts = 0, off_stats = 0, off_cst = 0, total = 0;
+  size_t off_abf = 0;                // BF16 row copies of the BF16 core pass (0 = none)
   size_t remap_bytes = 0;            // one of the two remapped coordinate copies
   int64_t rows = 0, grows = 0;      // sum I_n and sum I_n J_n
   // core-gradient kernel of the configured scheme (calculation or storage)
@@ -498,6 +499,9 @@ ft_status make_plan(int N, const int64_t *I, const int *J, int R, int64_t nnz, c
   p->off_stats = off; off += align_up(sizeof(float) * size_t(p->grows + 3 * p->rows));
   if (store) {
     p->off_cst = off; off += align_up(sizeof(float) * size_t(p->rows) * K);
+  }
+  if (c.precision == FT_BF16) {
+    p->off_abf = off; off += align_up(sizeof(uint16_t) * size_t(p->rows) * K);
   }
   p->total = off;
   return FT_OK;
@@ -927,6 +931,33 @@ ft_status ft_epoch_factors(ft_ctx *c, float lr_a, float lambda_a, const float *c
   return FT_OK;
 }
 
+struct RowsBf16Args {
+  const float *A[FT_MAXN];
+  uint32_t *out[FT_MAXN];       // row-major I_n x K/2 words
+  int J[FT_MAXN];
+  int64_t wbegin[FT_MAXN + 1];  // first word of mode n over all modes
+  int N, K;
+};
+
+// BF16 copy of every factor row for the BF16 core pass: row i of mode n
+// becomes K values (zeros past J_n), rounded to nearest even exactly as the
+// core pass rounds the float32 rows it gathers; one thread per word.
+__global__ void k_rows_bf16(const RowsBf16Args a) {
+  const int64_t total = a.wbegin[a.N];
+  for (int64_t w = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; w < total;
+       w += int64_t(gridDim.x) * blockDim.x) {
+    int n = 0;
+    while (n + 1 < a.N && w >= a.wbegin[n + 1]) ++n;
+    const int64_t local = w - a.wbegin[n];
+    const int64_t row = local / (a.K / 2);
+    const int j = 2 * int(local % (a.K / 2));
+    const float *src = a.A[n] + row * a.J[n];
+    const float lo = j < a.J[n] ? __ldg(src + j) : 0.f;
+    const float hi = j + 1 < a.J[n] ? __ldg(src + j + 1) : 0.f;
+    a.out[n][local] = ft::pack_bf16(lo, hi);
+  }
+}
+
 // Core gradient over the nonzeros [lo, hi) and, with update, the step
 // B <- B - lr_b (G / (hi - lo) + lambda_b B) (Algorithm 5 on that range).
 static ft_status core_pass(ft_ctx *c, float lr_b, float lambda_b, float *G_out, int update,
@@ -960,6 +991,29 @@ static ft_status core_pass(ft_ctx *c, float lr_b, float lambda_b, float *G_out, 
     const int64_t chunks = sa.chunk_begin[p.N];
     s = launch(c, reinterpret_cast<const void *>(&k_store_c), int((chunks + 255) / 256), 256, 0, &sa, st);
     if (s != FT_OK) return s;
+  }
+  if (p.off_abf != 0) {
+    // BF16 rows for the cooperative pass, made once per core phase (A does
+    // not change during it: later sets of ft_epoch_core_sgd reuse the copy)
+    RowsBf16Args ra;
+    memset(&ra, 0, sizeof(ra));
+    ra.N = p.N;
+    ra.K = p.K;
+    int64_t w = 0;
+    for (int n = 0; n < p.N; ++n) {
+      ra.A[n] = c->A[n];
+      ra.J[n] = p.J[n];
+      ra.out[n] = ws_ptr<uint32_t>(c, p.off_abf) + w;
+      ra.wbegin[n] = w;
+      a.abf[n] = ra.out[n];
+      w += p.I[n] * (p.K / 2);
+    }
+    ra.wbegin[p.N] = w;
+    if (lo == 0) {
+      const int grid = int(std::min<int64_t>((w + 255) / 256, int64_t(p.num_sms) * 16));
+      s = launch(c, reinterpret_cast<const void *>(&k_rows_bf16), grid, 256, 0, &ra, st);
+      if (s != FT_OK) return s;
+    }
   }
   s = launch(c, p.core_fn, p.grid_core, p.core_threads, p.core_smem, &a, st);
   if (s != FT_OK) return s;
@@ -1177,9 +1231,12 @@ ft_status ft_core_grad_noalloc(int N, const int64_t *I, const int *J, int R, int
   a.end = nnz;
   a.err = err;
   a.partial = reinterpret_cast<float *>(static_cast<char *>(scratch) + 256);
+  // the core pass that gathers float32 rows (no room for BF16 row copies);
+  // the same grid and order as the context's pass, so the same result
+  if (occupancy(p.ks.core_f32rows, p.ks.core_threads, p.ks.core_smem) < 1) return FT_ERR_CUDA;
   void *argv_core[] = {&a};
-  if (cudaLaunchKernel(p.ks.core, dim3(p.grid_core), dim3(p.ks.core_threads), argv_core, p.ks.core_smem, st) !=
-      cudaSuccess)
+  if (cudaLaunchKernel(p.ks.core_f32rows, dim3(p.grid_core), dim3(p.ks.core_threads), argv_core, p.ks.core_smem,
+                       st) != cudaSuccess)
     return FT_ERR_CUDA;
   FinalizeArgs f;
   memset(&f, 0, sizeof(f));

@@ -77,6 +77,9 @@ struct EpochArgs {
   // Storage scheme of the core pass: C^(n) = A^(n) B^(n) precomputed for
   // every row, row-major I_n x K (columns >= R are zero), or null.
   const float *cst[FT_MAXN];
+  // BF16 copies of A^(n) read by the BF16 core pass (k_core_coop with
+  // ROWS16): rows of K values, zeros past J_n, two values per word.
+  const uint32_t *abf[FT_MAXN];
 };
 
 // Mode of a cache slot.
@@ -291,13 +294,18 @@ struct Prod<K, MATH_BF16> {
     }
   }
   __device__ static void run(const float (&x)[2][CPL], const float *tabf, float (&y)[2][CPL], int lane) {
-    const uint2 *tab = reinterpret_cast<const uint2 *>(tabf);
     uint32_t xa[2][CPL / 2];
 #pragma unroll
     for (int q = 0; q < CPL / 2; ++q) {
       xa[0][q] = pack_bf16(x[0][2 * q], x[0][2 * q + 1]);
       xa[1][q] = pack_bf16(x[1][2 * q], x[1][2 * q + 1]);
     }
+    run_packed(xa, tabf, y, lane);
+  }
+  // x already rounded: word q of row h holds its columns CPL*t + 2q, + 1
+  __device__ static void run_packed(const uint32_t (&xa)[2][CPL / 2], const float *tabf, float (&y)[2][CPL],
+                                    int lane) {
+    const uint2 *tab = reinterpret_cast<const uint2 *>(tabf);
 #pragma unroll
     for (int u = 0; u < NT; ++u) {
       float acc[4] = {0.f, 0.f, 0.f, 0.f};
@@ -361,6 +369,23 @@ __device__ __forceinline__ void store_chunk(float *__restrict__ An, int64_t row,
   }
 }
 
+// The lane's chunk of row `row` of a BF16 row copy (rows of K values, two per
+// word): K/8 words, zeros when !valid.
+template <int K>
+__device__ __forceinline__ void load_chunk_bf16(const uint32_t *__restrict__ Abf, int64_t row, int t,
+                                                bool valid, uint32_t (&v)[K / 8]) {
+  const uint32_t *src = Abf + row * (K / 2) + (K / 8) * t;
+  if constexpr (K == 16) {
+    uint2 w = make_uint2(0u, 0u);
+    if (valid) w = __ldg(reinterpret_cast<const uint2 *>(src));
+    v[0] = w.x; v[1] = w.y;
+  } else {
+    uint4 w = make_uint4(0u, 0u, 0u, 0u);
+    if (valid) w = __ldg(reinterpret_cast<const uint4 *>(src));
+    v[0] = w.x; v[1] = w.y; v[2] = w.z; v[3] = w.w;
+  }
+}
+
 // Coordinates and values of one warp tile (loaded a tile ahead of use).
 template <int N>
 struct TileCoords {
@@ -408,8 +433,9 @@ struct Front {
   }
 
   // Decode the coordinates (bounds, cache slots) and gather the rows.
+  // rows = false: decode only (the caller reads the rows from elsewhere).
   __device__ __forceinline__ void gather(const EpochArgs &p, const TileCoords<N> &tc, int lane,
-                                         const float *rep = nullptr) {
+                                         const float *rep = nullptr, bool rows = true) {
     const int t = lane & 3;
     hot = 0u;
 #pragma unroll
@@ -451,6 +477,7 @@ struct Front {
 #pragma unroll
     for (int h = 0; h < 2; ++h)
       if (!valid[h]) x[h] = 0.f;
+    if (!rows) return;
 #pragma unroll
     for (int n = 0; n < N; ++n)
 #pragma unroll
@@ -1007,7 +1034,10 @@ __device__ __forceinline__ void coop_store(unsigned char *dst, const uint32_t (&
 }
 
 // STORE: the storage scheme (rows of C read from p.cst, Sec. 5.6).
-template <int N, int K, bool STORE = false>
+// ROWS16: the rows come from the BF16 copies p.abf (half the bytes of the
+// float32 rows); otherwise the float32 rows are gathered and rounded here, to
+// the same values.
+template <int N, int K, bool STORE = false, bool ROWS16 = false>
 __global__ void __launch_bounds__(32 * CoopSmem<N, K>::WARPS, CoopSmem<N, K>::MINB) k_core_coop(const EpochArgs p) {
   using L = CoopSmem<N, K>;
   static_assert(CoopProd<K>::WORDS == Prod<K, MATH_BF16>::WORDS, "one table size for both C paths");
@@ -1045,17 +1075,21 @@ __global__ void __launch_bounds__(32 * CoopSmem<N, K>::WARPS, CoopSmem<N, K>::MI
     // phase 1: this warp's 16 nonzeros (masked ones leave zero rows)
     {
       Front<N, K, MATH_BF16, true> f;
-      f.gather(p, cur, lane);
+      f.gather(p, cur, lane, nullptr, !ROWS16);
       // the raw rows go to shared memory as BF16 right away (the operand of
-      // both products), so that they need no registers afterwards
+      // both products)
+      uint32_t av[N][2][CPL / 2];
 #pragma unroll
       for (int n = 0; n < N; ++n)
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
-          uint32_t av[CPL / 2];
+          if constexpr (ROWS16) {
+            load_chunk_bf16<K>(p.abf[n], f.row[n][h], t, f.valid[h], av[n][h]);
+          } else {
 #pragma unroll
-          for (int q = 0; q < CPL / 2; ++q) av[q] = pack_bf16(f.a[n][h][2 * q], f.a[n][h][2 * q + 1]);
-          coop_store<CPL>(abuf + n * L::BUF + (FT_TILE * w + g + 8 * h) * L::LDB + 2 * CPL * t, av);
+            for (int q = 0; q < CPL / 2; ++q) av[n][h][q] = pack_bf16(f.a[n][h][2 * q], f.a[n][h][2 * q + 1]);
+          }
+          coop_store<CPL>(abuf + n * L::BUF + (FT_TILE * w + g + 8 * h) * L::LDB + 2 * CPL * t, av[n][h]);
         }
       if constexpr (STORE) {
         f.load_stored(p, lane);
@@ -1066,7 +1100,9 @@ __global__ void __launch_bounds__(32 * CoopSmem<N, K>::WARPS, CoopSmem<N, K>::MI
           CoopProd<K>::run(abuf_s + n * L::BUF + FT_TILE * w * L::LDB, L::LDB, smem + n * TW, f.c[n], lane);
         f.predict();
       } else {
-        f.compute(smem, TW, lane);
+#pragma unroll
+        for (int n = 0; n < N; ++n) Prod<K, MATH_BF16>::run_packed(av[n], smem + n * TW, f.c[n], lane);
+        f.predict();
       }
       float ne[2];
 #pragma unroll
@@ -1159,9 +1195,16 @@ __global__ void __launch_bounds__(256) k_eval(const EpochArgs p) {
   const int64_t nwarps = (int64_t(gridDim.x) * blockDim.x) >> 5;
   const int64_t ntiles = (p.end - p.begin + FT_TILE - 1) / FT_TILE;
   double se = 0.0, ae = 0.0;
+  // the next tile's coordinates and values are loaded before the current
+  // tile's rows, so the stream's DRAM latency overlaps the gathers
+  TileCoords<N> cur, nxt;
+  if (warp < ntiles) cur.load(p, p.begin + warp * FT_TILE, lane, MODE == 1);
   for (int64_t tile = warp; tile < ntiles; tile += nwarps) {
+    const int64_t next = tile + nwarps;
+    if (next < ntiles) nxt.load(p, p.begin + next * FT_TILE, lane, MODE == 1);
     Front<N, K, MATH_TF32X3, true> f;
-    f.load(p, p.begin + tile * FT_TILE, lane, MODE == 1);
+    f.gather(p, cur, lane);
+    cur = nxt;
     f.compute(smem, TW, lane);
     if ((lane & 3) == 0) {
 #pragma unroll

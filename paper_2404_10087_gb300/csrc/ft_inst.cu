@@ -45,7 +45,7 @@ ft::KernelSet make_set() {
   s.batch_core_smem = ft::CoreSmem<N, FT_K, FT_KMATH>::bytes();
   s.batch_core_threads = 32 * ft::CoreSmem<N, FT_K, FT_KMATH>::WARPS;
 #if FT_MATH == 2
-  s.core_store = reinterpret_cast<const void *>(&ft::k_core_coop<N, FT_K, true>);
+  s.core_store = reinterpret_cast<const void *>(&ft::k_core_coop<N, FT_K, true, true>);
   s.core_store_smem = ft::CoopSmem<N, FT_K>::bytes();
   s.core_store_threads = 32 * ft::CoopSmem<N, FT_K>::WARPS;
 #else
@@ -54,10 +54,14 @@ ft::KernelSet make_set() {
   s.core_store_threads = 32 * ft::CoreSmem<N, FT_K, FT_KMATH>::WARPS;
 #endif
 #if FT_MATH == 2
-  // BF16: the CTA-cooperative core pass
-  s.core = reinterpret_cast<const void *>(&ft::k_core_coop<N, FT_K>);
+  // BF16: the CTA-cooperative core pass on the BF16 row copies; the caller
+  // without a workspace (no room for the copies) gathers the float32 rows
+  s.core = reinterpret_cast<const void *>(&ft::k_core_coop<N, FT_K, false, true>);
   s.core_smem = ft::CoopSmem<N, FT_K>::bytes();
   s.core_threads = 32 * ft::CoopSmem<N, FT_K>::WARPS;
+  s.core_f32rows = reinterpret_cast<const void *>(&ft::k_core_coop<N, FT_K, false, false>);
+#else
+  s.core_f32rows = s.core;
 #endif
 #if FT_K == 16 && FT_MATH == 2
   if constexpr (N <= 4) {

@@ -11,6 +11,9 @@ struct KernelSet {
   const void *factor = nullptr;        // Hogwild factor pass
   const void *factor_delta = nullptr;  // deterministic factor pass (writes per-nonzero steps)
   const void *core = nullptr;          // core-gradient pass
+  // the same pass without the BF16 row copies of the workspace (gathers the
+  // float32 rows; equal results); `core` itself at FP32 and TF32
+  const void *core_f32rows = nullptr;
   size_t factor_smem = 0;              // tables only; the hot-row cache adds to it
   size_t core_smem = 0;
   int core_threads = 256;

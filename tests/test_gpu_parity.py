@@ -152,6 +152,23 @@ def test_core_gradient(shape, precision, scheme):
             assert rel_fro(G[n], ref[n]) <= 1e-5, n
 
 
+@pytest.mark.parametrize("shape", SHAPES, ids=SHAPE_IDS)
+def test_bf16_row_copies_change_nothing(shape):
+    """The BF16 core pass of a context reads BF16 copies of the factor rows
+    (rounded to nearest even, zero past J_n); the pass without a workspace
+    gathers the float32 rows and rounds them itself.  Same grid, same order,
+    same roundings: the gradients must be equal bit for bit."""
+    I, J, R, nnz = shape
+    idx, x, A, B = synth.random_problem(13, I, J, R, nnz)
+    gidx, gx, gA, gB = to_dev(idx, x, A, B)
+    m = ft.FastTuckerPlus(gidx, gx, gA, gB, precision="bf16")
+    G = torch.cat([g.reshape(-1) for g in m.core_grad()])
+    G2 = torch.empty_like(G)
+    ft.ft_core_grad_noalloc(gidx, gx, gA, gB, G2, precision="bf16")
+    torch.cuda.synchronize()
+    assert torch.equal(G, G2)
+
+
 @pytest.mark.parametrize("precision,scheme", [("fp32", "calc"), ("bf16", "calc"), ("fp32", "store"),
                                               ("bf16", "store")])
 def test_core_epoch_and_errors(precision, scheme):
