@@ -61,6 +61,14 @@ def peak_hbm():
         return FALLBACK_HBM_GBS, "fallback"
 
 
+def describe_data(w) -> str:
+    """The "data" field of the JSON line: how the workload's inputs were drawn."""
+    coords = f"Zipf({w.zipf_s}) coordinates" if w.dist == "zipf" else "uniform coordinates"
+    values = ("planted-model ratings 1..5" if w.ratings
+              else f"planted-model values + N(0, {w.noise_std}) noise")
+    return f"synthetic (seeded {coords}, {values}; {w.name})"
+
+
 def kernel_digest():
     h = hashlib.sha256()
     for name in ("ft_device.cuh",):
@@ -392,7 +400,7 @@ def run_ours(args, rank, world, local_rank):
         "scaling": "weak",
         "vs_baseline": None,
         "dtype": {"fp32": "f32", "tf32": "tf32", "bf16": "bf16"}[args.precision],
-        "data": "synthetic (seeded Zipf coordinates, planted-model ratings; Netflix-shaped)",
+        "data": describe_data(w),
         "config": {
             "workload": args.workload if args.nnz is None else f"{args.workload} at {args.nnz} coordinates", "N": N, "I": list(w.I), "J": J, "R": R,
             "nnz_train": nnz_train, "nnz_test": nnz_test, "precision": args.precision,
