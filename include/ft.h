@@ -75,7 +75,11 @@ typedef enum {
  * (each operand split into a TF32 head and tail, x = hi + lo, and the
  * product taken as lo.hi + hi.lo + hi.hi).  FT_TF32 and FT_BF16 round the
  * inputs of every contraction to TF32 or BF16 (tensor cores).  Predictions
- * and test errors are FP32-accurate in every mode. */
+ * and test errors are FP32-accurate in every mode.  An FT_BF16 context also
+ * keeps BF16 copies of the factor rows in its workspace (sum_n I_n * K * 2
+ * bytes), written at the start of every core phase and gathered by the core
+ * pass in place of the float32 rows (the same roundings, so the same
+ * results). */
 enum { FT_FP32 = 0, FT_TF32 = 1, FT_BF16 = 2 };
 
 /* How the factor phase writes rows back.
