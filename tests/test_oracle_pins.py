@@ -16,6 +16,9 @@ fixes independently of the oracle's code:
 * invariants: batch size does not matter when no two nonzeros share a row; a
   duplicated nonzero doubles the batch step; at an exact planted model with
   lambda = 0 nothing moves and with lambda > 0 rows only shrink;
+* the intermediates of one nonzero (c^(n), d^(n), p^(n) = d^(n) B^(n)T, xhat)
+  equal dense predictions of reduced models, and p^(n) equals the finite-
+  difference gradient of xhat with respect to a^(n);
 * hand-worked scalar examples (tests/golden/hand_worked.json);
 * RMSE/MAE by their definitions with math.fsum;
 * planted-model recovery.
@@ -97,6 +100,49 @@ def pin_factor_grad_fd(seed=1):
                         vals.append(0.5 * e * e + 0.5 * lam * np.dot(Ap[n][row], Ap[n][row]))
                     fd[j] = (vals[0] - vals[1]) / (2 * h)
                 np.testing.assert_allclose(g[n], fd, rtol=1e-6, atol=1e-7)
+
+
+def pin_nonzero_terms_dense(seed=13):
+    """Every intermediate of one nonzero against the dense model (Eq. "tucker"
+    with the Kruskal core), never against the oracle's own formulas:
+      * c^(n)_r is the dense prediction of a model that keeps column r of
+        B^(n) and replaces every other mode by the scalar 1 (J_k = R = 1);
+      * d^(n)_r is the dense prediction of the rank-1 model made of column r
+        of every B^(k), with mode n replaced by the scalar 1;
+      * p^(n) = d^(n) B^(n)T is the gradient of xhat with respect to a^(n)
+        (central differences through the dense model);
+      * xhat = a^(n) . p^(n) for every n (xhat is linear in each a^(n)) and
+        equals the dense prediction."""
+    rng = np.random.default_rng(seed)
+    h = 1e-6
+    one_a, one_b = np.ones((1, 1)), np.ones((1, 1))
+    for N, J, R in [(3, (2, 3, 4), 3), (4, (2, 2, 3, 2), 4), (2, (3, 1), 2), (1, (3,), 2)]:
+        I = [4 + n for n in range(N)]
+        A, B, idx, _ = rand_problem(rng, N, I, J, R, 4)
+        for m in range(idx.shape[1]):
+            c, d, p, xhat = oracle.nonzero_terms(A, B, idx, m)
+            coord = idx[:, m]
+            assert math.isclose(xhat, dense_predict(A, B, coord), rel_tol=1e-12, abs_tol=1e-13)
+            for n in range(N):
+                for r in range(R):
+                    As = [A[k] if k == n else one_a for k in range(N)]
+                    Bs = [B[k][:, [r]] if k == n else one_b for k in range(N)]
+                    cs = [coord[k] if k == n else 0 for k in range(N)]
+                    assert math.isclose(c[n, r], dense_predict(As, Bs, cs), rel_tol=1e-12, abs_tol=1e-13)
+                    As = [one_a if k == n else A[k] for k in range(N)]
+                    Bs = [one_b if k == n else B[k][:, [r]] for k in range(N)]
+                    cs = [0 if k == n else coord[k] for k in range(N)]
+                    assert math.isclose(d[n, r], dense_predict(As, Bs, cs), rel_tol=1e-12, abs_tol=1e-13)
+                fd = np.empty(J[n])
+                for j in range(J[n]):
+                    vals = []
+                    for sgn in (+1, -1):
+                        Ap = [a.copy() for a in A]
+                        Ap[n][coord[n], j] += sgn * h
+                        vals.append(dense_predict(Ap, B, coord))
+                    fd[j] = (vals[0] - vals[1]) / (2 * h)
+                np.testing.assert_allclose(p[n], fd, rtol=1e-6, atol=1e-8)
+                assert math.isclose(float(np.dot(A[n][coord[n]], p[n])), xhat, rel_tol=1e-12, abs_tol=1e-13)
 
 
 def pin_core_grad_fd(seed=2):
@@ -378,7 +424,7 @@ def pin_planted_recovery(seed=11):
     assert r1 < 0.05 * r0, (r0, r1)
 
 
-PINS = [pin_predict_dense, pin_factor_grad_fd, pin_core_grad_fd, pin_core_epoch_step, pin_core_sgd_sets,
+PINS = [pin_predict_dense, pin_nonzero_terms_dense, pin_factor_grad_fd, pin_core_grad_fd, pin_core_epoch_step, pin_core_sgd_sets,
         pin_cp_special_case, pin_mf_special_case, pin_full_batch_is_sum_of_fd_grads,
         pin_disjoint_rows_batch_invariance, pin_duplicate_doubles_step,
         pin_planted_fixed_point, pin_hand_worked, pin_errors_definition, pin_planted_recovery]
@@ -404,6 +450,9 @@ MUTANTS = [
     ("update_sign_flipped", "a[j] -= gamma * s * g[j];", "a[j] += gamma * s * g[j];"),
     ("mae_squared", "ae += fabs(e);", "ae += e * e;"),
     ("core_sgd_values_of_first_set", "x + lo, gamma, lambda, nthreads);", "x, gamma, lambda, nthreads);"),
+    ("back_projection_uses_c_not_d",
+     "for (int r = 0; r < R; ++r) s += d[n * R + r] * B[n][(int64_t)j * R + r];\n      p[off + j] = s;",
+     "for (int r = 0; r < R; ++r) s += c[n * R + r] * B[n][(int64_t)j * R + r];\n      p[off + j] = s;"),
     ("core_sgd_first_set_only", "for (int64_t lo = 0; lo < nnz; lo += S) {",
      "for (int64_t lo = 0; lo < nnz && lo < S; lo += S) {"),
 ]
