@@ -88,6 +88,7 @@ def _declare(lib):
         "orc_nonzero_terms": [_INT, _P, _INT, _P, _P, _P, _I64, _P, _P, _P, _P],
         "orc_factor_grads": [_INT, _P, _INT, _P, _P, _P, _I64, _DBL, _DBL, _P],
         "orc_factor_epoch": [_INT, _P, _P, _INT, _P, _P, _I64, _P, _P, _I64, _DBL, _DBL, _P],
+        "orc_factor_epoch_hogwild": [_INT, _P, _INT, _P, _P, _I64, _P, _P, _DBL, _DBL, _INT],
         "orc_core_grad": [_INT, _P, _INT, _P, _P, _I64, _P, _P, _P, _INT],
         "orc_core_epoch": [_INT, _P, _INT, _P, _P, _I64, _P, _P, _DBL, _DBL, _INT],
         "orc_core_epoch_sgd": [_INT, _P, _INT, _P, _P, _I64, _P, _P, _I64, _DBL, _DBL, _INT],
@@ -203,6 +204,19 @@ def factor_epoch(A, B, idx, x, S: int, gamma: float, lam: float, row_scale=None)
                                    _ptr(xv), int(S), float(gamma), float(lam), prs),
            "orc_factor_epoch")
     del keep
+    return m.A
+
+
+def factor_epoch_hogwild(A, B, idx, x, gamma: float, lam: float, nthreads: int = 1):
+    """The factor epoch as Hogwild on `nthreads` host threads (S = 1 within a
+    thread, concurrent row updates may be lost): for timing the CPU baseline,
+    never as a parity reference.  Returns the new factor matrices."""
+    m = _Model([np.array(a, dtype=np.float64, copy=True) for a in A], B)
+    cols, pidx, nnz = _coords(idx, m.N)
+    xv = np.ascontiguousarray(x, dtype=np.float64)
+    _check(load().orc_factor_epoch_hogwild(m.N, _ptr(m.J), m.R, m.pA, m.pB, nnz, pidx, _ptr(xv),
+                                           float(gamma), float(lam), int(nthreads)),
+           "orc_factor_epoch_hogwild")
     return m.A
 
 

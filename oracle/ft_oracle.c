@@ -232,6 +232,71 @@ done:
 }
 
 /*
+ * Hogwild form of the factor epoch on nthreads host threads, for TIMING the
+ * CPU baseline only (it is not a parity reference: its result depends on
+ * the thread schedule).  Thread t takes the contiguous range
+ * [nnz t / T, nnz (t + 1) / T) of the stored order and applies the rule of
+ * Eq. "Update_FastTuckerPlus_factor" one nonzero at a time (S = 1), all N
+ * rows from the values it has just read, directly to the shared factor
+ * matrices, as the paper's kernel does on the GPU: concurrent updates of a
+ * row may be lost.  The shared entries are read and written with relaxed
+ * atomic loads and stores (plain loads and stores on x86-64 and aarch64), so
+ * the races are well defined.
+ */
+static double orc_ld(const double *p) {
+  double v;
+  __atomic_load(p, &v, __ATOMIC_RELAXED);
+  return v;
+}
+
+static void orc_st(double *p, double v) { __atomic_store(p, &v, __ATOMIC_RELAXED); }
+
+int orc_factor_epoch_hogwild(int N, const int *J, int R, double *const *A,
+                             double *const *B, int64_t nnz, const int32_t *const *idx,
+                             const double *x, double gamma, double lambda, int nthreads) {
+  if (orc_check_shape(N, J, R)) return ORC_EARG;
+  for (int n = 0; n < N; ++n)
+    if (J[n] > ORC_MAX_RANK) return ORC_EARG;
+  if (nthreads < 1) nthreads = 1;
+#ifdef _OPENMP
+#pragma omp parallel num_threads(nthreads)
+#endif
+  {
+    int tid = 0, nt = 1;
+#ifdef _OPENMP
+    tid = omp_get_thread_num();
+    nt = omp_get_num_threads();
+#endif
+    int64_t lo = nnz * tid / nt, hi = nnz * (tid + 1) / nt;
+    double a[ORC_MAX_ORDER * ORC_MAX_RANK];   /* the N rows as read */
+    double c[ORC_MAX_ORDER * ORC_MAX_RANK], d[ORC_MAX_ORDER * ORC_MAX_RANK];
+    for (int64_t m = lo; m < hi; ++m) {
+      for (int n = 0; n < N; ++n) {
+        const double *row = A[n] + (int64_t)idx[n][m] * J[n];
+        for (int j = 0; j < J[n]; ++j) a[n * ORC_MAX_RANK + j] = orc_ld(row + j);
+        for (int r = 0; r < R; ++r) {
+          double sum = 0.0;
+          for (int j = 0; j < J[n]; ++j) sum += a[n * ORC_MAX_RANK + j] * B[n][(int64_t)j * R + r];
+          c[n * R + r] = sum;
+        }
+      }
+      orc_d_rows(N, R, c, d);
+      double e = x[m] - orc_xhat(N, R, c);
+      for (int n = 0; n < N; ++n) {
+        double *row = A[n] + (int64_t)idx[n][m] * J[n];
+        for (int j = 0; j < J[n]; ++j) {
+          double dbt = 0.0;
+          for (int r = 0; r < R; ++r) dbt += d[n * R + r] * B[n][(int64_t)j * R + r];
+          const double av = a[n * ORC_MAX_RANK + j];
+          orc_st(row + j, av - gamma * (-e * dbt + lambda * av));
+        }
+      }
+    }
+  }
+  return ORC_OK;
+}
+
+/*
  * Core gradient summed over the training set (Algorithm 5 accumulation of
  * Eq. "Gradient_core_tensor_cp" without the regulariser):
  *     G^(n) = sum_m (xhat_m - x_m) a^(n)_{i_n}^T d^(n)        (J_n x R)

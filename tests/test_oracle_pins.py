@@ -478,3 +478,26 @@ def test_planted_mistakes_break_a_pin(tmp_path):
         if not caught:
             survivors.append(name)
     assert not survivors, f"planted mistakes no pin caught: {survivors}"
+
+
+def test_hogwild_timing_epoch_is_the_sequential_epoch():
+    """The host Hogwild epoch (timing of the CPU baseline only) runs the same
+    rule: on one thread it is the sequential epoch (S = 1) bit for bit, also
+    with rows shared by many nonzeros; on several threads, when no two
+    nonzeros share a row, it is again the sequential epoch bit for bit."""
+    rng = np.random.default_rng(14)
+    N, J, R = 3, (3, 4, 2), 3
+    A, B, idx, x = rand_problem(rng, N, [6, 5, 7], J, R, 60)
+    one = oracle.factor_epoch_hogwild(A, B, idx, x, 0.05, 0.1, nthreads=1)
+    seq = oracle.factor_epoch(A, B, idx, x, 1, 0.05, 0.1)
+    for n in range(N):
+        np.testing.assert_array_equal(one[n], seq[n])
+    nnz = 40
+    I = [nnz + 3, nnz + 1, nnz + 8]
+    A = [rng.normal(0, 0.5, (I[n], J[n])) for n in range(N)]
+    idx = np.stack([rng.permutation(I[n])[:nnz] for n in range(N)]).astype(np.int32)
+    x = rng.normal(0, 1, nnz)
+    many = oracle.factor_epoch_hogwild(A, B, idx, x, 0.05, 0.1, nthreads=4)
+    seq = oracle.factor_epoch(A, B, idx, x, 1, 0.05, 0.1)
+    for n in range(N):
+        np.testing.assert_array_equal(many[n], seq[n])
