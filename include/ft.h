@@ -99,10 +99,19 @@ typedef struct {
   /* FT_HOGWILD only: shared-memory write-back cache of the most frequent rows
    * of the tensor (ranked over all modes by their number of training
    * nonzeros).  Each CTA keeps hot_rows rows in shared memory, updates them
-   * there, and every hot_window CTA tiles (8 warps x 16 nonzeros) writes its
-   * dirty rows back (plain stores, so CTAs still race as in Hogwild) and
-   * refreshes its copy.  Only rows with at least hot_min_count training
-   * nonzeros are cached.  hot_rows: -1 = as many as 96 KB hold, 0 = off. */
+   * there, and every hot_window CTA tiles (8 warps x 16 nonzeros) adds its
+   * weighted change of every dirty row (cached row minus the copy it read at
+   * the last refresh) to the row in A with float atomics and refreshes its
+   * copy: no CTA overwrites another CTA's change, and a CTA sees the others'
+   * from its next refresh on.  The weight is 1 for a row that a CTA meets
+   * less than once between two write-backs (the CTAs' steps add up, as in
+   * Hogwild); a row that every CTA meets many times between two write-backs
+   * takes the average of the CTAs' changes (weight 1 / the CTAs expected to
+   * change it), since adding them would apply the same move once per CTA.
+   * The weights come from the row counts at ft_init.  The workspace holds
+   * each CTA's copy (CTAs x hot_rows x K floats).  Only rows with at least
+   * hot_min_count training nonzeros are cached.  hot_rows: -1 = as many as
+   * 96 KB hold, 0 = off. */
   int hot_rows;
   int hot_window;      /* >= 1; default 128 */
   int hot_min_count;   /* >= 1; default 2 */
@@ -264,7 +273,11 @@ ft_status ft_core_apply(ft_ctx *ctx, const float *G, int64_t nnz_total, float lr
  * exits.  Calls that would need more than that (more CTAs times N * K * K
  * partials than fit) return FT_ERR_WORKSPACE; on a GB300 every supported
  * shape fits.  The first call on a device looks up the array's device address
- * with that device current (make that first call before any stream capture).
+ * with that device current (make that first call before any stream capture)
+ * and keeps it for the process: a cudaDeviceReset of that device after the
+ * first call is not supported (the kept address would be stale).  Unlike
+ * ft_init, the call does not validate its inputs in a separate pass: the
+ * kernel masks and reports out-of-range coordinates and non-finite values.
  * Every call shares the array and overwrites it: calls that overlap on the
  * GPU (on different streams or host threads) race and corrupt each other's
  * results, so serialise them.
@@ -360,14 +373,16 @@ ft_status ft_rmse(ft_ctx *ctx, int64_t n, const int32_t *const *idx, const float
  *   rows, in/out; NULL = no history, ema = |g| / count);
  *   labels[r] (NULL = not computed): the exact line-search step along -g of
  *   the row's subproblem sum_m [1/2 (x_m - a.p_m)^2 + 1/2 lambda_a |a|^2],
- *   |g|^2 / (sum_m (p_m.g)^2 + lambda_a count |g|^2), divided by lr_a and
- *   clipped to [1/4, 4] (1 for rows without nonzeros).
+ *   |g|^2 / (sum_m (p_m.g)^2 + lambda_a count |g|^2), divided by lr_a,
+ *   clipped to [1/16, 16], as its natural log (the regression target of the
+ *   step-size network; 0 for rows without nonzeros).
  * FP32 with atomic accumulation (the summation order varies between runs). */
 ft_status ft_row_stats(ft_ctx *ctx, float lambda_a, float lr_a, float ema_beta, float *ema,
                        float *features, float *labels, void *stream);
 
 /* ------------------------------------------------------- step-size network
- * A small MLP (3 -> 64 -> 64 -> 1, ReLU, output s = 1/4 + 15/4 sigmoid(z))
+ * A small MLP (3 -> 64 -> 64 -> 1, ReLU, linear output u = the predicted
+ * log-multiplier; multiplier s = exp(clamp(u, log 1/16, log 16)))
  * that maps the row features of ft_row_stats to per-row step multipliers for
  * ft_epoch_factors (row_step_scale).  Not in the paper.  All state lives in
  * one caller-allocated device buffer of ft_stepnet_bytes() bytes (16-byte
@@ -377,7 +392,7 @@ ft_status ft_row_stats(ft_ctx *ctx, float lambda_a, float lr_a, float ema_beta, 
 size_t ft_stepnet_bytes(void);
 
 /* Initialise the buffer: He-uniform weights from a counter-based hash of
- * (seed, index), zero biases except b3 = log(1/4), so s starts near 1. */
+ * (seed, index), zero biases, so u starts near 0 and s near 1. */
 ft_status ft_stepnet_init(void *net, uint64_t seed, void *stream);
 
 /* scale[r] = s(features[3 r .. 3 r + 2]) for r < rows (device arrays). */
@@ -385,7 +400,9 @@ ft_status ft_stepnet_forward(const void *net, int64_t rows, const float *feature
                              void *stream);
 
 /* `steps` full-batch Adam steps (lr, betas 0.9 / 0.999, eps 1e-8) on the mean
- * of 1/2 (s - label)^2 over `rows` samples.  loss_out (host, nullable)
+ * of 1/2 (u - label)^2 over `rows` samples (labels: log-multipliers, as
+ * ft_row_stats writes them; the output is not clamped in the loss, so its
+ * gradient does not vanish).  loss_out (host, nullable)
  * receives the loss of the last step's forward pass (synchronises). */
 ft_status ft_stepnet_train(void *net, int64_t rows, const float *features, const float *labels,
                            float lr, int steps, double *loss_out, void *stream);

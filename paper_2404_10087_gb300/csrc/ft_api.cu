@@ -296,8 +296,9 @@ struct RowFinishArgs {
 
 // Features and labels of every row from the accumulated statistics:
 // f0 = log(1 + count), f1 = log(1 + ema of |g| / count), f2 = mean residual;
-// label = exact line-search step along -g of the row's subproblem divided by
-// the step size, clipped to [1/4, 4] (1 for rows without nonzeros).
+// label = log of the exact line-search step along -g of the row's subproblem
+// divided by the step size, clipped to [1/16, 16] (0 for rows without
+// nonzeros).
 __global__ void k_row_finish(const RowFinishArgs a) {
   const int64_t q = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (q >= a.roff[a.N]) return;
@@ -317,8 +318,8 @@ __global__ void k_row_finish(const RowFinishArgs a) {
   if (a.label) {
     float sc = 1.f;
     const float den = a.hsum[q] + a.lambda * k * gg;
-    if (k > 0.f && gg > 0.f && den > 0.f) sc = fminf(fmaxf(gg / den / a.gamma, 0.25f), 4.f);
-    a.label[q] = sc;
+    if (k > 0.f && gg > 0.f && den > 0.f) sc = fminf(fmaxf(gg / den / a.gamma, 1.f / 16.f), 16.f);
+    a.label[q] = logf(sc);
   }
 }
 
@@ -343,6 +344,8 @@ struct Plan {
   size_t off_order = 0, off_segptr = 0, off_segrow = 0;
   size_t off_remap = 0, off_hot = 0, off_counts = 0, off_stats = 0, off_cst = 0, total = 0;
   size_t off_abf = 0;                // BF16 row copies of the BF16 core pass (0 = none)
+  size_t off_snap = 0;               // per-CTA snapshots of the hot-row cache
+  size_t off_hotw = 0;               // write-back weight of every cache slot
   size_t remap_bytes = 0;            // one of the two remapped coordinate copies
   int64_t rows = 0, grows = 0;      // sum I_n and sum I_n J_n
   // core-gradient kernel of the configured scheme (calculation or storage)
@@ -481,6 +484,9 @@ ft_status make_plan(int N, const int64_t *I, const int *J, int R, int64_t nnz, c
     p->off_remap = off;  off += 2 * p->remap_bytes;
     p->off_hot = off;    off += align_up(sizeof(int32_t) * size_t(p->hot_cap));
     p->off_counts = off; off += align_up(sizeof(int32_t) * size_t(sumI));
+    const int snap_ctas = std::max(p->grid_factor, p->grid_factor_tc);
+    p->off_snap = off;   off += align_up(sizeof(float) * size_t(snap_ctas) * p->hot_cap * K);
+    p->off_hotw = off;   off += align_up(sizeof(float) * size_t(p->hot_cap));
   }
   if (c.scatter == FT_DETERMINISTIC) {
     p->det_S = std::max<int64_t>(1, std::min<int64_t>(c.det_batch, std::max<int64_t>(nnz, 1)));
@@ -742,6 +748,24 @@ ft_status build_hot_cache(ft_ctx *c, cudaStream_t st) {
   std::sort(cand.begin(), cand.end(), [](const Cand &a, const Cand &b) {
     return a.n != b.n ? a.n < b.n : a.r < b.r;
   });
+  // Write-back weight of every slot.  A CTA handles n_w nonzeros between two
+  // write-backs (hot_window CTA tiles of 128 nonzeros, or its whole share of
+  // a small tensor).  A row with c of the nnz nonzeros appears x = c n_w /
+  // nnz times in that share, and P = G (1 - (1 - c / nnz)^n_w) of the G CTAs
+  // are expected to change it between write-backs.  x < 1: the CTAs' changes
+  // are distinct steps of distinct nonzeros and add up (w = 1, Hogwild);
+  // x >= 1: every CTA moves the row several steps toward the same optimum
+  // and the row takes their average (w = 1 / P).
+  const int G = p.cfg.engine == FT_ENGINE_TCGEN05 ? p.grid_factor_tc : p.grid_factor;
+  const double n_w = std::min<double>(double(p.cfg.hot_window) * 128.0,
+                                      std::ceil(double(p.nnz) / double(std::max(G, 1))));
+  std::vector<float> weight(std::max<size_t>(k, 1), 1.f);
+  for (size_t q = 0; q < k; ++q) {
+    const double cnt = double(cand[q].count), nnz = double(std::max<int64_t>(p.nnz, 1));
+    const double x = cnt * n_w / nnz;
+    const double P = double(G) * -std::expm1(n_w * std::log1p(-std::min(cnt / nnz, 1.0 - 1e-12)));
+    weight[q] = x >= 1.0 ? float(1.0 / std::max(1.0, P)) : 1.f;
+  }
   std::vector<int32_t> hot(std::max<size_t>(k, 1), 0);
   int64_t mode_off[FT_MAXN + 1] = {0};
   for (int n = 0; n < p.N; ++n) mode_off[n + 1] = mode_off[n] + p.I[n];
@@ -757,6 +781,8 @@ ft_status build_hot_cache(ft_ctx *c, cudaStream_t st) {
   int32_t *d_hot = ws_ptr<int32_t>(c, p.off_hot);
   if (cudaMemcpyAsync(d_hot, hot.data(), sizeof(int32_t) * hot.size(), cudaMemcpyHostToDevice, st) !=
           cudaSuccess ||
+      cudaMemcpyAsync(ws_ptr<float>(c, p.off_hotw), weight.data(), sizeof(float) * k, cudaMemcpyHostToDevice,
+                      st) != cudaSuccess ||
       cudaMemcpyAsync(d_counts, slot_of.data(), sizeof(int32_t) * sumI, cudaMemcpyHostToDevice, st) !=
           cudaSuccess)
     return FT_ERR_CUDA;
@@ -887,6 +913,8 @@ ft_status ft_epoch_factors(ft_ctx *c, float lr_a, float lambda_a, const float *c
       a.hot_rows = ws_ptr<int32_t>(c, p.off_hot);
       a.hot_cap = p.hot_cap;
       a.hot_window = p.cfg.hot_window;
+      a.hot_snap = ws_ptr<float>(c, p.off_snap);
+      a.hot_weight = ws_ptr<float>(c, p.off_hotw);
     }
     if (p.cfg.engine == FT_ENGINE_TCGEN05)
       return launch(c, p.ks.factor_tc, p.grid_factor_tc, p.ks.factor_tc_threads,

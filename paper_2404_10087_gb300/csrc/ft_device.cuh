@@ -74,6 +74,12 @@ struct EpochArgs {
   int hot_base[FT_MAXN + 1];
   int hot_cap;                      // slots in shared memory (0 = no cache)
   int hot_window;                   // CTA tiles between write-back/refresh
+  // Per-CTA copy of the cached rows as the CTA last read them from global
+  // memory ([grid][hot_cap][K] floats, workspace): the write-back adds the
+  // CTA's own change (cache - copy), times the slot's weight, instead of
+  // storing the row.
+  float *hot_snap;
+  const float *hot_weight;          // per slot (see build_hot_cache)
   // Storage scheme of the core pass: C^(n) = A^(n) B^(n) precomputed for
   // every row, row-major I_n x K (columns >= R are zero), or null.
   const float *cst[FT_MAXN];
@@ -585,10 +591,25 @@ __device__ __forceinline__ void fill_tables(float *smem, const EpochArgs &p, boo
   }
 }
 
-// Hot-row cache traffic (whole CTA): refresh every slot from L2, or write the
-// dirty slots back and clear their flags.
+// Hot-row cache traffic (whole CTA).  Refresh: copy every slot from L2 into
+// the cache and into the CTA's snapshot (global, private to the CTA).
+// Write-back: for every dirty slot add w_slot (cache - snapshot) - the CTA's
+// own change of the row since the refresh, weighted - to the global row with
+// float atomics, then clear the flags.  No CTA overwrites another CTA's
+// change.  w_slot = 1 (Hogwild: the CTAs' steps add up) for rows a CTA meets
+// less than once per window; for rows every CTA meets many times per window
+// w_slot = 1 / (CTAs expected to change the row in one window), so the row
+// moves by the average of the CTAs' changes (parameter averaging): each CTA
+// has run the row toward the same optimum on its own share of the data, and
+// their sum would overshoot it by that many times.
+template <int K>
+__device__ __forceinline__ float *cta_snapshot(const EpochArgs &p) {
+  return p.hot_snap + size_t(blockIdx.x) * size_t(p.hot_cap) * K;
+}
+
 template <int N, int K>
 __device__ void cache_refresh(const EpochArgs &p, float *rep) {
+  float *snap = cta_snapshot<K>(p);
   for (int e = threadIdx.x; e < p.hot_cap * (K / 4); e += blockDim.x) {
     const int slot = e / (K / 4), j0 = 4 * (e % (K / 4));
     const int n = slot_mode(p, slot, N);
@@ -605,24 +626,29 @@ __device__ void cache_refresh(const EpochArgs &p, float *rep) {
       }
     }
     *reinterpret_cast<float4 *>(rep + size_t(slot) * K + j0) = v;
+    __stcg(reinterpret_cast<float4 *>(snap + size_t(slot) * K + j0), v);
   }
 }
 
 template <int N, int K>
 __device__ void cache_write_back(const EpochArgs &p, const float *rep, unsigned char *dirty) {
+  const float *snap = cta_snapshot<K>(p);
   for (int e = threadIdx.x; e < p.hot_cap * (K / 4); e += blockDim.x) {
     const int slot = e / (K / 4), j0 = 4 * (e % (K / 4));
     const int n = slot_mode(p, slot, N);
     if (slot >= p.hot_base[N] || j0 >= p.J[n] || !dirty[slot]) continue;
     const float4 v = *reinterpret_cast<const float4 *>(rep + size_t(slot) * K + j0);
+    const float4 s = __ldcg(reinterpret_cast<const float4 *>(snap + size_t(slot) * K + j0));
+    const float w = __ldg(p.hot_weight + slot);
+    const float4 d = make_float4(w * (v.x - s.x), w * (v.y - s.y), w * (v.z - s.z), w * (v.w - s.w));
     float *dst = p.A[n] + int64_t(__ldg(p.hot_rows + slot)) * p.J[n] + j0;
     if (((p.vecmask >> n) & 1) != 0) {
-      __stcg(reinterpret_cast<float4 *>(dst), v);
+      atomicAdd(reinterpret_cast<float4 *>(dst), d);
     } else {
-      __stcg(dst, v.x);
-      if (j0 + 1 < p.J[n]) __stcg(dst + 1, v.y);
-      if (j0 + 2 < p.J[n]) __stcg(dst + 2, v.z);
-      if (j0 + 3 < p.J[n]) __stcg(dst + 3, v.w);
+      atomicAdd(dst, d.x);
+      if (j0 + 1 < p.J[n]) atomicAdd(dst + 1, d.y);
+      if (j0 + 2 < p.J[n]) atomicAdd(dst + 2, d.z);
+      if (j0 + 3 < p.J[n]) atomicAdd(dst + 3, d.w);
     }
   }
   __syncthreads();
@@ -706,8 +732,11 @@ __device__ __forceinline__ void factor_tile(const EpochArgs &p, const float *tab
 // the hottest lines.  So the hottest rows of every mode (chosen at ft_init
 // from the row counts) live in a per-CTA write-back cache in shared memory:
 // the CTA's warps read and update the cached copy, and every hot_window CTA
-// tiles the CTA writes its dirty rows back to global memory (plain stores,
-// so concurrent CTAs still race as in Hogwild) and refreshes its copy.
+// tiles the CTA adds its weighted change of every dirty row to global memory
+// (float atomics, so no CTA overwrites another's change; see
+// cache_write_back) and refreshes its copy.
+// Rows outside the cache are stored back with plain stores: concurrent
+// updates of one of them may be lost, as in the paper's kernel.
 // Coordinates of cached rows arrive remapped to -(slot + 1); the slots are
 // shared by all modes and go to the most frequent rows of the tensor.
 //
@@ -881,6 +910,7 @@ __global__ void __launch_bounds__(256) k_core(const EpochArgs p) {
     if constexpr (STORE) f.load_stored(p, lane);
     else f.compute(smem, TW, lane);
     const float ne0 = f.xhat[0] - f.x[0], ne1 = f.xhat[1] - f.x[1];
+    if (__any_sync(FULL, !isfinite(ne0) || !isfinite(ne1)) && lane == 0) atomicOr(p.err, ERRBIT_NONFINITE);
 #pragma unroll
     for (int n = 0; n < N; ++n) {
       float d[2][CPL];

@@ -76,15 +76,29 @@ def test_no_alloc_fits_the_largest_shapes(precision):
         assert rel_fro(got, ref) <= 1e-5, (len(I), J[0])
 
 
-def test_no_alloc_reports_bad_coordinates():
-    idx, x, A, B = problem(23, (10, 11, 12), (4, 4, 4), 4, 100)
+@pytest.mark.parametrize("precision", ["fp32", "tf32", "bf16"])
+@pytest.mark.parametrize("shape", [((10, 11, 12), (4, 4, 4), 4, 100), ((10, 11, 12, 13), (32, 20, 8, 32), 24, 16 * 9 + 5)],
+                         ids=["K16", "K32"])
+def test_no_alloc_reports_bad_inputs(precision, shape):
+    """This entry point skips the validation pass of ft_init, so the kernel
+    itself must mask and report a coordinate outside [0, I_n) (FT_ERR_INDEX)
+    and a non-finite value (FT_ERR_NONFINITE); the error word is cleared by
+    the next call, whose result is then exact."""
+    I, J, R, nnz = shape
+    idx, x, A, B = problem(23, I, J, R, nnz)
+    out = torch.empty(sum(J) * R, dtype=torch.float32, device=DEV)
     bad = [t.clone() for t in idx]
-    bad[2][5] = 12  # == I_3
-    out = torch.empty(3 * 4 * 4, dtype=torch.float32, device=DEV)
+    bad[2][5] = I[2]
     with pytest.raises(ft.FtError) as e:
-        ft.ft_core_grad_noalloc(bad, x, A, B, out)
+        ft.ft_core_grad_noalloc(bad, x, A, B, out, precision=precision)
     assert e.value.status == -2
-    # the error word is cleared by the next call
-    ft.ft_core_grad_noalloc(idx, x, A, B, out)
-    ref = with_context(idx, x, A, B, "fp32")
+    ref = with_context(idx, x, A, B, precision)
+    ft.ft_core_grad_noalloc(idx, x, A, B, out, precision=precision)
+    assert rel_fro(out.double().cpu().numpy(), ref) <= 1e-5
+    xn = x.clone()
+    xn[7] = float("nan")
+    with pytest.raises(ft.FtError) as e:
+        ft.ft_core_grad_noalloc(idx, xn, A, B, out, precision=precision)
+    assert e.value.status == -5
+    ft.ft_core_grad_noalloc(idx, x, A, B, out, precision=precision)
     assert rel_fro(out.double().cpu().numpy(), ref) <= 1e-5
