@@ -13,8 +13,9 @@ hot-row cache).
     CTA-cooperative core pass; FP32: the generic one) equals the sum of the
     gradients over the two halves of the nonzeros (a property of the sum at
     any size: 1e-5 relative), and the gradient over the first 4e6 training
-    nonzeros matches the oracle (BF16 within 2e-2 x (N - 1) / 2, the small
-    parity tests' tolerance, FP32 within 1e-5, Frobenius norm per mode);
+    nonzeros matches the oracle (FP32 within 1e-5 in Frobenius norm per
+    mode; FP32 1e-5 and BF16 2e-2 elementwise against the absolute-value
+    model of the gradient, as in the small parity tests);
   * one core epoch moves B by exactly the step its own gradient gives;
   * the test-set RMSE and MAE over all 2e7 test nonzeros against the oracle
     (<= 1e-5);
@@ -34,7 +35,7 @@ pytestmark = [pytest.mark.gpu, pytest.mark.slow]
 DEV = "cuda:0"
 THREADS = oracle.default_threads()
 N = 4
-BF16_TOL = 2e-2 * (N - 1) / 2
+BF16_TOL = 2e-2
 
 
 def rel_fro(got, ref):
@@ -89,9 +90,16 @@ SLICE = 4_000_000
 
 @pytest.fixture(scope="module")
 def oracle_grad_slice(full):
+    """The oracle's gradient over the first SLICE training nonzeros and its
+    absolute-value model (the gradient's terms on |A|, |B| and |e|)."""
     idx = np.ascontiguousarray(full["tr_h"][:, :SLICE])
-    return oracle.core_grad(f64(full["A0"]), f64(full["B0"]), idx, full["x_tr"][:SLICE].double().numpy(),
-                            nthreads=THREADS)
+    A64, B64 = f64(full["A0"]), f64(full["B0"])
+    x = full["x_tr"][:SLICE].double().numpy()
+    G = oracle.core_grad(A64, B64, idx, x, nthreads=THREADS)
+    e = x - oracle.predict(A64, B64, idx, nthreads=THREADS)
+    Aa, Ba = [np.abs(a) for a in A64], [np.abs(b) for b in B64]
+    shifted = oracle.predict(Aa, Ba, idx, nthreads=THREADS) - np.abs(e)
+    return G, oracle.core_grad(Aa, Ba, idx, shifted, nthreads=THREADS)
 
 
 def grad_over(full, precision, lo, hi):
@@ -114,8 +122,11 @@ def test_order4_core_gradient_and_epoch(full, oracle_grad_slice, precision, tol)
     for n in range(N):
         assert rel_fro(G[n], G1[n] + G2[n]) <= 1e-5, n
     Gs = grad_over(full, precision, 0, SLICE)
+    ref, scale = oracle_grad_slice
     for n in range(N):
-        assert rel_fro(Gs[n], oracle_grad_slice[n]) <= tol, n
+        assert np.max(np.abs(Gs[n] - ref[n]) / np.maximum(scale[n], 1e-300)) <= tol, n
+        if precision == "fp32":
+            assert rel_fro(Gs[n], ref[n]) <= 1e-5, n
     lr, lam = 0.01, 0.01
     m.epoch_core(lr, lam)
     for n in range(N):

@@ -1,19 +1,23 @@
 """GPU path against the FP64 oracle, through the C ABI.
 
-Tolerances (relative; denominators as stated):
+Tolerances (relative; denominators as stated), the same at every order N:
   * FP32 path: predictions <= 1e-5 relative to the same model evaluated on
     |A|, |B| (the scale of the FP32 rounding bound, so cancellation does not
-    count against the kernel) and <= 1e-5 in Frobenius norm; core gradients
-    <= 1e-5 elementwise relative to the absolute-value model of the
-    gradient and in Frobenius norm; one deterministic factor
-    epoch's factors <= 1e-4 (Frobenius per matrix) and its step
-    A_new - A_old <= 1e-4; one core epoch's B <= 1e-5.
-  * TF32 path: steps (Frobenius) and gradients (absolute-value model) <= 5e-3.
-  * BF16 path: the same at <= 2e-2; trained test RMSE within 1% of the
-    FP64 oracle's.
-  * TF32 and BF16 bounds hold for N <= 3 and grow by (N - 1) / 2 above
-    (the leave-one-out product has N - 1 rounded factors).
-Sizes span several 16-nonzero tiles with a ragged tail.
+    count against the kernel) and <= 1e-5 in Frobenius norm; per-nonzero
+    factor gradients and factor steps <= 1e-5 elementwise against the
+    absolute-value error model of tests/errmodel.py, and <= 1e-5 elementwise
+    relative to max(|step|, RMS step of the mode) (or 10 times the step
+    change that rounding A, B to the precision's inputs causes in the
+    oracle, if larger: see TOL_ELEM_RMS); core gradients <= 1e-5
+    elementwise relative to the absolute-value model of the gradient and in
+    Frobenius norm; one deterministic factor epoch's factors <= 1e-4
+    (Frobenius per matrix); one core epoch's B <= 1e-5.
+  * TF32 path: the elementwise factor bounds at 5e-3, gradients
+    (absolute-value model) <= 5e-3.
+  * BF16 path: the same at 2e-2; trained test RMSE within 1% of the FP64
+    oracle's.
+Factors and cores are zero-mean draws at every order.  Sizes span several
+16-nonzero tiles with a ragged tail.
 """
 import math
 
@@ -21,6 +25,7 @@ import numpy as np
 import pytest
 import torch
 
+import errmodel
 import oracle
 from paper_2404_10087_gb300 import ft, synth
 
@@ -29,14 +34,15 @@ pytestmark = pytest.mark.gpu
 DEV = "cuda:0"
 TOL_STEP = {"fp32": 1e-4, "tf32": 5e-3, "bf16": 2e-2}
 TOL_GRAD = {"fp32": 1e-5, "tf32": 5e-3, "bf16": 2e-2}
-
-
-def order_factor(precision, N):
-    """Growth of the TF32/BF16 tolerances with the order: D^(n) multiplies
-    N - 1 rounded products a.B, so its relative rounding error grows about
-    linearly in N - 1; the stated tolerances hold for N <= 3 and scale by
-    (N - 1) / 2 above.  FP32 keeps its bounds (its rounding is 2^-24)."""
-    return 1.0 if precision == "fp32" else max(1.0, (N - 1) / 2)
+# elementwise factor steps: against the absolute-value error model (the
+# stated bounds), and relative to max(|step|, RMS step of the mode) within
+# the larger of TOL_ELEM_RMS and 10 times the change that a rounding of A and
+# B to the precision's inputs causes in the FP64 oracle's own step (the
+# error the inputs' precision implies by itself; on zero-mean factors of
+# high order it exceeds any fixed bound, since d^(n) multiplies N - 1
+# products that can cancel)
+TOL_ELEM_MODEL = {"fp32": 1e-5, "tf32": 5e-3, "bf16": 2e-2}
+TOL_ELEM_RMS = {"fp32": 1e-5, "tf32": 5e-3, "bf16": 2e-2}
 
 
 def to_dev(idx, x, A, B):
@@ -109,27 +115,68 @@ def test_predict_fp32(shape):
     assert rel_fro(got, ref) <= 1e-5
 
 
+def check_factor_step(A0, B, idx, x, S, lr, lam, A1, precision):
+    """Elementwise check of one factor epoch's step A1 - A0 against the
+    oracle's batch-synchronous epoch (batch S): against the absolute-value
+    error model and relative to max(|step|, RMS step of the mode); rows no
+    nonzero touches are unchanged bit for bit.  Returns both errors."""
+    ref, scales, touches = errmodel.epoch_step_model(A0, B, idx, x, S, lr, lam)
+    for a0, a1, t in zip(A0, A1, touches):
+        assert np.array_equal(a1[t == 0], a0[t == 0])
+    em = errmodel.step_errors(A0, A1, ref, scales, touches)
+    er = errmodel.step_errors_floor(A0, A1, ref, touches, 1.0)
+    sens = errmodel.rounding_sensitivity(A0, B, idx, x, S, lr, lam, errmodel.UNIT_ROUNDOFF[precision])
+    assert em <= TOL_ELEM_MODEL[precision], em
+    assert er <= max(TOL_ELEM_RMS[precision], 10 * sens), (er, sens)
+    return em, er
+
+
+def collision_free(shape, seed):
+    """The shape's ranks and nonzero count with mode sizes of at least nnz and
+    rows that no two nonzeros share in any mode."""
+    I, J, R, nnz = shape
+    I2 = tuple(max(In, nnz + 3) for In in I)
+    _, x, A, B = synth.random_problem(seed, I2, J, R, nnz)
+    g = torch.Generator().manual_seed(seed + 1000)
+    idx = torch.stack([torch.randperm(In, generator=g)[:nnz] for In in I2]).to(torch.int32)
+    return idx, x, A, B
+
+
+@pytest.mark.parametrize("precision", ["fp32", "tf32", "bf16"])
+@pytest.mark.parametrize("shape", SHAPES, ids=SHAPE_IDS)
+def test_per_nonzero_gradients(shape, precision):
+    """Eq. "Gradient_low_rank_cp" per nonzero, element by element: with rows
+    that no two nonzeros share and one batch of all nonzeros, the
+    deterministic epoch at step 1 moves every row by exactly -g of its one
+    nonzero, computed from the starting factors."""
+    idx, x, A, B = collision_free(shape, 21)
+    gidx, gx, gA, gB = to_dev(idx, x, A, B)
+    nnz = shape[3]
+    m = ft.FastTuckerPlus(gidx, gx, gA, gB, precision=precision, scatter="deterministic", det_batch=nnz)
+    m.epoch_factors(1.0, 0.05)
+    m.check()
+    check_factor_step(f64(A), f64(B), idx.numpy(), x.double().numpy(), nnz, 1.0, 0.05, f64(gA), precision)
+
+
 @pytest.mark.parametrize("precision", ["fp32", "tf32", "bf16"])
 @pytest.mark.parametrize("shape", SHAPES, ids=SHAPE_IDS)
 def test_deterministic_factor_epoch(shape, precision):
+    """One batch-synchronous epoch (batch 128, rows shared by many nonzeros):
+    the step element by element, and at FP32 the factors in Frobenius norm."""
     I, J, R, nnz = shape
-    # At N >= 9, zero-mean factors make some of the N - 1 rounded products in
-    # D^(n) cancel to near zero (TF32/BF16 step errors of 4.5e-2 / 1e-1 at
-    # N = 10, FP32 unaffected); non-negative draws test the rounding alone.
-    idx, x, A, B = synth.random_problem(2, I, J, R, nnz, positive=len(I) >= 9)
+    idx, x, A, B = synth.random_problem(2, I, J, R, nnz)
     gidx, gx, gA, gB = to_dev(idx, x, A, B)
     S = 128
     lr, lam = 0.02, 0.05
     m = ft.FastTuckerPlus(gidx, gx, gA, gB, precision=precision, scatter="deterministic", det_batch=S)
     m.epoch_factors(lr, lam)
     m.check()
-    ref = oracle.factor_epoch(f64(A), f64(B), idx.numpy(), x.double().numpy(), S, lr, lam)
     got = f64(gA)
-    A0 = f64(A)
-    for n in range(len(I)):
-        if precision == "fp32":
+    check_factor_step(f64(A), f64(B), idx.numpy(), x.double().numpy(), S, lr, lam, got, precision)
+    if precision == "fp32":
+        ref = oracle.factor_epoch(f64(A), f64(B), idx.numpy(), x.double().numpy(), S, lr, lam)
+        for n in range(len(I)):
             assert rel_fro(got[n], ref[n]) <= 1e-4
-        assert rel_fro(got[n] - A0[n], ref[n] - A0[n]) <= TOL_STEP[precision] * order_factor(precision, len(I)), n
 
 
 @pytest.mark.parametrize("scheme", ["calc", "store"])
@@ -147,7 +194,7 @@ def test_core_gradient(shape, precision, scheme):
     ref = oracle.core_grad(A64, B64, i64, x64)
     scale = core_grad_scale(A64, B64, i64, x64)
     for n in range(len(I)):
-        assert rel_bound(G[n], ref[n], scale[n]) <= TOL_GRAD[precision] * order_factor(precision, len(I)), n
+        assert rel_bound(G[n], ref[n], scale[n]) <= TOL_GRAD[precision], n
         if precision == "fp32":
             assert rel_fro(G[n], ref[n]) <= 1e-5, n
 
@@ -208,7 +255,7 @@ def test_core_sgd_sets_match_oracle(shape, precision, scheme):
     ref = oracle.core_epoch_sgd(f64(A), f64(B), idx.numpy(), x.double().numpy(), S, lr, lam)
     got, B0 = f64(gB), f64(B)
     for n in range(len(I)):
-        assert rel_fro(got[n] - B0[n], ref[n] - B0[n]) <= TOL_GRAD[precision] * order_factor(precision, len(I)), n
+        assert rel_fro(got[n] - B0[n], ref[n] - B0[n]) <= TOL_GRAD[precision], n
 
 
 def test_core_sgd_one_set_is_the_core_epoch():
@@ -236,10 +283,13 @@ def test_row_step_scale_deterministic():
     scales = [torch.rand(In, generator=g, dtype=torch.float64).float() * 3.75 + 0.25 for In in I]
     m = ft.FastTuckerPlus(gidx, gx, gA, gB, scatter="deterministic", det_batch=64)
     m.epoch_factors(0.02, 0.05, [s.to(DEV) for s in scales])
-    ref = oracle.factor_epoch(f64(A), f64(B), idx.numpy(), x.double().numpy(), 64, 0.02, 0.05,
-                              row_scale=[s.double().numpy() for s in scales])
-    for n in range(3):
-        assert rel_fro(f64(gA)[n] - f64(A)[n], ref[n] - f64(A)[n]) <= 1e-4
+    m.check()
+    rs = [s.double().numpy() for s in scales]
+    A0 = f64(A)
+    ref, sc, touches = errmodel.epoch_step_model(A0, f64(B), idx.numpy(), x.double().numpy(), 64, 0.02, 0.05,
+                                                 row_scale=rs)
+    assert errmodel.step_errors(A0, f64(gA), ref, sc, touches) <= TOL_ELEM_MODEL["fp32"]
+    assert errmodel.step_errors_floor(A0, f64(gA), ref, touches, 1.0) <= 1e-4
 
 
 @pytest.mark.parametrize("cache", [dict(hot_rows=0), dict(hot_min_count=1), dict(hot_min_count=1, hot_window=1)],
@@ -260,9 +310,8 @@ def test_hogwild_without_collisions_is_exact(precision, cache, nnz):
     m = ft.FastTuckerPlus(gidx, gx, gA, gB, precision=precision, **cache)
     m.epoch_factors(0.03, 0.02)
     m.check()
-    ref = oracle.factor_epoch(f64(A), f64(B), idx.numpy(), x.double().numpy(), 1, 0.03, 0.02)
-    for n in range(3):
-        assert rel_fro(f64(gA)[n] - f64(A)[n], ref[n] - f64(A)[n]) <= TOL_STEP[precision]
+    # no shared rows: the sequential epoch equals one batch of all nonzeros
+    check_factor_step(f64(A), f64(B), idx.numpy(), x.double().numpy(), nnz, 0.03, 0.02, f64(gA), precision)
 
 
 def test_permute_reorders_the_epoch():
@@ -456,21 +505,25 @@ def test_planted_training_matches_oracle(precision, tol):
     assert abs(g - o) <= tol * o, (g, o)
 
 
-@pytest.mark.parametrize("hot_rows", [-1, 0], ids=["cache", "no_cache"])
+@pytest.mark.parametrize("cache,band", [(dict(hot_rows=3000, hot_min_count=1), 0.02), (dict(hot_rows=-1), 0.10),
+                                        (dict(hot_rows=0), 0.35)], ids=["all_rows_cached", "cache", "no_cache"])
 @pytest.mark.parametrize("precision", ["fp32", "bf16"])
-def test_hogwild_training_converges(precision, hot_rows):
-    """The Hogwild pass (concurrent row updates may be lost) still trains:
-    ten epochs lower the test RMSE and stay within 35% of the sequential
-    FP64 oracle's.  (This tensor is small - 9e4 nonzeros on 1000 rows per
-    mode - so tens of thousands of concurrent updates collide.)"""
+def test_hogwild_training_converges(precision, cache, band):
+    """The Hogwild pass on a tensor whose rows collide constantly (9e4
+    nonzeros on 1000 rows per mode, tens of thousands of updates in flight):
+    ten epochs lower the test RMSE, and end near the sequential FP64 oracle's.
+    With every row in the shared-memory cache no update is lost (each CTA's
+    change is added to the row at write-back), and the run ends within 2% of
+    the sequential oracle; with the default cache (the 1512 most frequent
+    rows) within 10%; without the cache, where concurrent plain stores of a
+    row lose updates as in the paper's kernel, within 35%."""
     w, d, x, A0, B0 = planted_setup()
     tr, te = d.train, d.test
     gA = [a.clone().to(DEV) for a in A0]
     gB = [b.clone().to(DEV) for b in B0]
     tri = [d.idx[n, tr].contiguous().to(DEV) for n in range(3)]
     tei = [d.idx[n, te].contiguous().to(DEV) for n in range(3)]
-    m = ft.FastTuckerPlus(tri, x[tr].contiguous().to(DEV), gA, gB, precision=precision,
-                          hot_rows=hot_rows)
+    m = ft.FastTuckerPlus(tri, x[tr].contiguous().to(DEV), gA, gB, precision=precision, **cache)
     lr = lam = 0.01
     oA, oB = f64(A0), f64(B0)
     itr, ite = d.idx[:, tr].numpy(), d.idx[:, te].numpy()
@@ -484,7 +537,7 @@ def test_hogwild_training_converges(precision, hot_rows):
     g = m.rmse(tei, x[te].contiguous().to(DEV))[0]
     o = oracle.errors(oA, oB, ite, xte)[0]
     assert g < r0, (g, r0)
-    assert g <= 1.35 * o, (g, o)
+    assert abs(g - o) <= band * o, (g, o)
 
 
 # ------------------------------------------------------------ edge cases
