@@ -118,20 +118,23 @@ def normal_matrices(gen: torch.Generator, shapes, std: float, device="cpu",
     ]
 
 
-def uniform_matrices(gen: torch.Generator, shapes, hi: float, device="cpu",
-                     dtype=torch.float32):
-    return [
-        (torch.rand(tuple(sh), generator=gen, device=device, dtype=torch.float64) * hi).to(dtype)
-        for sh in shapes
-    ]
+def start_std(J: int, R: int, N: int, pred_std: float = 0.2) -> float:
+    """Standard deviation s of an N(0, s^2) start for every entry of A^(n) and
+    B^(n) whose predictions have standard deviation ``pred_std``: each
+    a^(n) B^(n) entry has variance J s^4 and the prediction sums R products of
+    N of them, so pred_std^2 = R (J s^4)^N.  A small random start: at much
+    smaller ones plain SGD stalls near the saddle point at zero."""
+    return (pred_std * pred_std / R) ** (1.0 / (4 * N)) / J ** 0.25
 
 
-def rating_scale_init(J: int, R: int, N: int, mean_value: float) -> float:
-    """Upper end s of a U(0, s) initialisation whose expected prediction is
-    about ``mean_value`` for ratings-valued tensors: each of the N factor/core
-    products averages J*s^2/4 and the prediction sums R products of N of them."""
-    per_mode = (mean_value / R) ** (1.0 / N)
-    return math.sqrt(4.0 * per_mode / J)
+def centre(train_x: torch.Tensor, *others: torch.Tensor):
+    """Values minus the training mean (computed in float64): the mean and the
+    centred training values, then every other tensor centred by the same
+    mean.  Ratings tensors are trained centred, since the model
+    sum_r prod_n c^(n)_r has no offset term."""
+    mu = float(train_x.double().mean()) if train_x.numel() else 0.0
+    return (mu, (train_x.double() - mu).to(torch.float32),
+            *[(t.double() - mu).to(torch.float32) for t in others])
 
 
 def to_ratings(pred: torch.Tensor, centre: float = 3.0, spread: float = 1.1,
@@ -179,6 +182,11 @@ WORKLOADS = {
     "planted_uniform_1e5": Workload(
         name="planted_uniform_1e5", I=(1000, 1000, 1000), nnz=100_000, J=(4, 4, 4), R=4,
         dist="uniform", planted_std=0.5, noise_std=0.1),
+    # the same planted model on Zipf-skewed coordinates (row counts spread
+    # over orders of magnitude)
+    "planted_zipf_1e5": Workload(
+        name="planted_zipf_1e5", I=(1000, 1000, 1000), nnz=100_000, J=(4, 4, 4), R=4,
+        dist="zipf", zipf_s=1.1, planted_std=0.5, noise_std=0.1),
     "netflix_shaped_zipf_1e8": Workload(
         name="netflix_shaped_zipf_1e8", I=(480_000, 18_000, 2_200), nnz=100_000_000,
         J=(16, 16, 16), R=16, dist="zipf", zipf_s=1.1, planted_std=0.25, ratings=True),
@@ -233,17 +241,18 @@ def draw_workload(w: Workload, device="cpu", nnz: int | None = None) -> Draw:
                 train=train, test=test)
 
 
-def initial_factors(w: Workload, device="cpu", mean_value: float | None = None, seed_offset: int = 1):
-    """Starting point of training: N(0, 1/sqrt(J)) for planted real-valued
-    tensors, U(0, s) sized to the mean rating for ratings tensors."""
+def initial_factors(w: Workload, device="cpu", seed_offset: int = 1):
+    """Starting point of training, N(0, s^2) entries: s = 1/sqrt(J) for
+    planted real-valued tensors; for ratings tensors (trained centred, unit
+    scale) the s of ``start_std``, whose predictions have standard deviation
+    0.2."""
     gen = generator(w.seed + seed_offset, device)
     if w.ratings:
-        hi = rating_scale_init(max(w.J), w.R, w.N, 3.0 if mean_value is None else mean_value)
-        A = [uniform_matrices(gen, [(I, J)], hi, device)[0] for I, J in zip(w.I, w.J)]
-        B = [uniform_matrices(gen, [(J, w.R)], hi, device)[0] for J in w.J]
+        sd = [start_std(max(w.J), w.R, w.N)] * w.N
     else:
-        A = [normal_matrices(gen, [(I, J)], 1.0 / math.sqrt(J), device)[0] for I, J in zip(w.I, w.J)]
-        B = [normal_matrices(gen, [(J, w.R)], 1.0 / math.sqrt(J), device)[0] for J in w.J]
+        sd = [1.0 / math.sqrt(J) for J in w.J]
+    A = [normal_matrices(gen, [(I, J)], s, device)[0] for I, J, s in zip(w.I, w.J, sd)]
+    B = [normal_matrices(gen, [(J, w.R)], s, device)[0] for J, s in zip(w.J, sd)]
     return A, B
 
 

@@ -44,8 +44,8 @@ def full():
     tr, te = d.train.cpu(), d.test.cpu()
     tr_h = np.ascontiguousarray(idx_h[:, tr.numpy()])
     te_h = np.ascontiguousarray(idx_h[:, te.numpy()])
-    x_tr, x_te = vals[tr].contiguous(), vals[te].contiguous()
-    A0, B0 = synth.initial_factors(w, mean_value=float(x_tr.double().mean()))
+    _, x_tr, x_te = synth.centre(vals[tr].contiguous(), vals[te].contiguous())
+    A0, B0 = synth.initial_factors(w)
     return dict(w=w, tr_h=tr_h, te_h=te_h, x_tr=x_tr, x_te=x_te, A0=A0, B0=B0,
                 tri=[torch.from_numpy(tr_h[n]).to(DEV) for n in range(3)],
                 tei=[torch.from_numpy(te_h[n]).to(DEV) for n in range(3)],
