@@ -26,6 +26,7 @@ import sys
 import threading
 import time
 
+import numpy as np
 import torch
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
@@ -36,11 +37,13 @@ from paper_2404_10087_gb300 import ft, synth  # noqa: E402
 METRIC = "SGD nonzero-updates/sec (factor+core) at J=R=16; time-to-RMSE vs plain FP32"
 UNIT = "nnz-updates/s"
 WORKLOAD = "netflix_shaped_zipf_1e8"
-# Step sizes of the Netflix-shaped workload (the paper's are unstated), picked
-# by a short sweep for a smooth test-RMSE curve; the core step is on the scale
-# of a full-gradient step because Algorithm 5 divides the summed gradient by
-# |Omega|.
-LR = 0.005         # factor step gamma_A
+# Step sizes of the Netflix-shaped workload (the paper's are unstated): a
+# sweep of the factor step on the full tensor (FP32, 20 epochs; test RMSE
+# 0.005: 0.94, 0.01: 0.80, 0.02: 0.61, 0.03: 0.58, 0.04: 0.577, 0.06: 0.562,
+# 0.08 and 0.12 diverged) - 0.04 keeps a factor of two to the first step that
+# diverged; the core step is on the scale of a full-gradient step because
+# Algorithm 5 divides the summed gradient by |Omega|.
+LR = 0.04          # factor step gamma_A
 LR_B = 0.3         # core step gamma_B
 LAM = 0.01
 FALLBACK_HBM_GBS = 6800.0
@@ -186,7 +189,9 @@ def make_workload(device, nnz=None, name=WORKLOAD):
     test_idx = [d.idx[n, te].contiguous() for n in range(N)]
     train_x = vals[tr].contiguous()
     test_x = vals[te].contiguous()
-    A, B = synth.initial_factors(w, device=device, mean_value=float(train_x.double().mean()))
+    if w.ratings:   # trained centred: the model has no offset term
+        _, train_x, test_x = synth.centre(train_x, test_x)
+    A, B = synth.initial_factors(w, device=device)
     return w, train_idx, train_x, test_idx, test_x, A, B
 
 
@@ -206,6 +211,10 @@ def one_allocation(mats):
 
 
 BATCHED = "batched_64"
+# Step sizes of the batched workload (planted real-valued tensors; none are
+# given for it): the learned-step configuration's eta = lambda = 0.01 for the
+# factors, the Netflix-shaped workload's core step
+LR_BATCH, LR_B_BATCH = 0.01, 0.3
 
 
 def run_batched(args, rank, world, local_rank):
@@ -233,7 +242,7 @@ def run_batched(args, rank, world, local_rank):
     stream = torch.cuda.current_stream(dev)
     b = ft.FastTuckerBatch(train, precision=args.precision, tune=True)
     for _ in range(args.warmup):
-        b.epoch(LR, LAM, LR_B, LAM)
+        b.epoch(LR_BATCH, LAM, LR_B_BATCH, LAM)
     torch.cuda.synchronize()
     if world > 1:
         torch.distributed.barrier()
@@ -242,7 +251,7 @@ def run_batched(args, rank, world, local_rank):
         t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         t0.record(stream)
         for _ in range(args.steps):
-            b.epoch(LR, LAM, LR_B, LAM)
+            b.epoch(LR_BATCH, LAM, LR_B_BATCH, LAM)
         t1.record(stream)
         torch.cuda.synchronize()
     total_ms = t0.elapsed_time(t1)
@@ -251,19 +260,62 @@ def run_batched(args, rank, world, local_rank):
     (total_ms,), value = aggregate_replicas([total_ms], nnz_train, args.steps, world, dev)
     if rank != 0:
         return None
-    return {
+    # algorithmic bytes of one epoch, summed over the tensors: the factor
+    # phase (coordinates, value, N rows read and written) and the core phase
+    # (coordinates, value, N rows read) of every training nonzero
+    epoch_bytes = sum(int(t[1].numel()) * (algorithmic_bytes_factor(len(t[0]), [a.shape[1] for a in t[2]])
+                                           + 4 * len(t[0]) + 4 + 4 * sum(a.shape[1] for a in t[2]))
+                      for t in train)
+    peak, peak_kind = peak_hbm()
+    ms_per_step = total_ms / args.steps
+    achieved = epoch_bytes / (ms_per_step / 1e3) / 1e9
+    out = {
         "metric": METRIC + " (batched: 64 tensors, one graph per epoch)", "value": value, "unit": UNIT,
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": {"fp32": "f32", "tf32": "tf32", "bf16": "bf16"}[args.precision],
         "data": "synthetic (64 planted tensors of uneven order, size and rank, uniform coordinates)",
         "config": {"workload": BATCHED, "tensors": 64, "nnz_train": nnz_train, "precision": args.precision,
-                   "classes": b.classes(), "lr_a": LR, "lr_b": LR_B, "lambda": LAM,
+                   "classes": b.classes(), "lr_a": LR_BATCH, "lr_b": LR_B_BATCH, "lambda": LAM,
                    "l2": "inputs larger than L2 (training COO 216 MB per epoch)"},
         "mean_test_rmse": sum(rm) / len(rm),
+        "roofline": {"bound": "hbm", "kernel": "the epoch graph (factor + core kernels of every class, "
+                                                "finalize)", "scope": "epoch",
+                     "achieved": achieved, "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": None, "bytes_per_epoch": epoch_bytes,
+                     "launch_ms": ms_per_step},
         "gpu_launches": int(launches),
         "clocks": clk.summary(),
     }
+    if not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline_batched(train)
+    return out
+
+
+def cpu_baseline_batched(train, budget_s=10.0):
+    """The FP64 oracle on every host core over the batch's tensors, one after
+    another (Hogwild factor epoch + core epoch each), until about `budget_s`
+    seconds of work; the rate over the tensors timed is taken as the batch's."""
+    import oracle
+    threads = oracle.default_threads()
+    done, secs, ntens = 0, 0.0, 0
+    for idx, x, A, B in train:
+        i64 = np.ascontiguousarray(torch.stack([t.cpu() for t in idx]).numpy())
+        x64 = x.double().cpu().numpy()
+        A64 = [a.double().cpu().numpy() for a in A]
+        B64 = [b.double().cpu().numpy() for b in B]
+        t = time.perf_counter()
+        A64 = oracle.factor_epoch_hogwild(A64, B64, i64, x64, LR_BATCH, LAM, nthreads=threads)
+        oracle.core_epoch(A64, B64, i64, x64, LR_B_BATCH, LAM, nthreads=threads)
+        secs += time.perf_counter() - t
+        done += int(x.numel())
+        ntens += 1
+        if secs >= budget_s:
+            break
+    return {"value": done / secs, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": f"the first {ntens} of {len(train)} tensors ({done} training nonzeros), one FP64 "
+                      f"Hogwild factor epoch + core epoch each on {threads} host threads, {secs:.1f} s; "
+                      f"rate taken as the batch's"}
 
 
 def run_ours(args, rank, world, local_rank):
@@ -501,7 +553,7 @@ def run_sweep(args, local_rank):
         base = None
         for R, J in ((16, 16), (16, 32), (32, 16), (32, 32)):
             w = synth.Workload(**{**w0.__dict__, "J": (J,) * w0.N, "R": R})
-            A, B = synth.initial_factors(w, device=dev, mean_value=float(trx.double().mean()))
+            A, B = synth.initial_factors(w, device=dev)
             eng = engine_for(args, w0.N, J, R)
             m = ft.FastTuckerPlus(tri, trx, A, B, precision=args.precision, hot_rows=args.hot_rows,
                                   hot_window=args.hot_window, engine=eng)
@@ -572,65 +624,34 @@ def run_sweep(args, local_rank):
             "data": "synthetic", "rows": rows}
 
 
-def learned_step_ab(dev, epochs=20, lr=0.01, lam=0.01):
-    """Planted 3-order tensor (1e5 uniform coordinates, planted J = R = 4, noise
-    0.1), eta = lambda = 0.01 for factors and cores: epochs and wall time for
-    the learned per-row step size to reach the plain FP32 method's test RMSE
-    after `epochs` epochs.  The network is trained on traces of a plain run
-    from another start; its statistics and network passes are timed."""
+def learned_step_ab(dev, epochs=20, lam=0.01, lr_b=0.01,
+                    lrs=(0.005, 0.01, 0.02, 0.04, 0.08, 0.16, 0.32)):
+    """The planted 3-order tensor (1e5 coordinates, planted J = R = 4, noise
+    0.1) with uniform coordinates (the learned-step configuration) and with
+    Zipf(1.1) coordinates: lambda = 0.01, core step 0.01, the learned per-row
+    step against plain FP32 SGD at fixed factor steps `lrs` (eta* = the
+    lowest test RMSE after `epochs` epochs); see learned_step.ab_study."""
     from paper_2404_10087_gb300 import learned_step as ls
-    w = synth.WORKLOADS["planted_uniform_1e5"]
-    d = synth.draw_workload(w, device=dev)
-    allidx = [d.idx[n].contiguous() for n in range(w.N)]
-    pm = ft.FastTuckerPlus(allidx, torch.zeros(d.idx.shape[1], device=dev),
-                           [a.contiguous() for a in d.planted_A], [b.contiguous() for b in d.planted_B], hot_rows=0)
-    x = pm.predict(allidx) + d.noise
-    pm.close()
-    tri = [d.idx[n, d.train].contiguous() for n in range(w.N)]
-    tei = [d.idx[n, d.test].contiguous() for n in range(w.N)]
-    xtr, xte = x[d.train].contiguous(), x[d.test].contiguous()
+    out = {}
+    for name in ("planted_uniform_1e5", "planted_zipf_1e5"):
+        w = synth.WORKLOADS[name]
+        d = synth.draw_workload(w, device=dev)
+        allidx = [d.idx[n].contiguous() for n in range(w.N)]
+        pm = ft.FastTuckerPlus(allidx, torch.zeros(d.idx.shape[1], device=dev),
+                               [a.contiguous() for a in d.planted_A], [b.contiguous() for b in d.planted_B],
+                               hot_rows=0)
+        x = pm.predict(allidx) + d.noise
+        pm.close()
+        tri = [d.idx[n, d.train].contiguous() for n in range(w.N)]
+        tei = [d.idx[n, d.test].contiguous() for n in range(w.N)]
+        xtr, xte = x[d.train].contiguous(), x[d.test].contiguous()
 
-    def start(off):
-        return synth.initial_factors(w, device=dev, seed_offset=off)
+        def make_model(start, w=w, tri=tri, xtr=xtr):
+            A, B = synth.initial_factors(w, device=dev, seed_offset=start)
+            return ft.FastTuckerPlus(tri, xtr, A, B)
 
-    def timed(step, model, target=None):
-        curve = [model.rmse(tei, xte)[0]]
-        torch.cuda.synchronize()
-        t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        t0.record()
-        r, ep = None, 0
-        for ep in range(1, epochs + 1):
-            step()
-            r = model.rmse(tei, xte)[0]
-            curve.append(r)
-            if target is not None and r <= target:
-                break
-        t1.record()
-        t1.synchronize()
-        timed.curves.append([round(v, 5) for v in curve])
-        return ep, t0.elapsed_time(t1) / 1e3, r
-
-    timed.curves = []
-
-    A, B = start(1)
-    plain = ft.FastTuckerPlus(tri, xtr, A, B)
-    ep_p, t_p, target = timed(lambda: (plain.epoch_factors(lr, lam), plain.epoch_core(lr, lam)), plain)
-    A, B = start(7)
-    feats, labels = ls.collect_traces(ft.FastTuckerPlus(tri, xtr, A, B), 10, lr, lam, lr, lam)
-    net = ft.new_stepnet(dev, seed=0)
-    curve = ls.train(net, feats, labels, steps=400, lr=3e-3)
-    A, B = start(1)
-    model = ft.FastTuckerPlus(tri, xtr, A, B)
-    learned = ls.LearnedStep(model, net, lr, lam)
-    ep_l, t_l, r_l = timed(lambda: learned.epoch(lr, lam), model, target)
-    reached = r_l <= target
-    return {"workload": "planted_uniform_1e5", "target_test_rmse": target, "plain_epochs": ep_p,
-            "plain_seconds": t_p, "learned_epochs": ep_l if reached else None,
-            "learned_seconds": t_l if reached else None, "reached": reached,
-            "speedup": (t_p / t_l) if reached else None, "trace_rows": int(labels.numel()),
-            "net_train_loss": [round(v, 5) for v in curve],
-            "plain_curve": timed.curves[0], "learned_curve": timed.curves[1],
-            "mean_multiplier": float(learned.scale.mean())}
+        out[name] = ls.ab_study(make_model, tei, xte, lrs, lam, lr_b, lam, epochs=epochs)
+    return out
 
 
 def time_to_rmse(w, tri, trx, tei, tex, dev, epochs, precision, window=3):
@@ -641,7 +662,7 @@ def time_to_rmse(w, tri, trx, tei, tex, dev, epochs, precision, window=3):
     'strict' = the FP32 run's final window mean after `epochs` epochs, and
     'within_1pct' = 1.01 x that.  An epoch is factor phase + core phase + test
     RMSE; times are CUDA events from the start of the run."""
-    A0, B0 = synth.initial_factors(w, device=dev, mean_value=float(trx.double().mean()))
+    A0, B0 = synth.initial_factors(w, device=dev)
 
     def run(prec, n_epochs):
         A = [a.clone() for a in A0]
@@ -690,7 +711,6 @@ def time_to_rmse(w, tri, trx, tei, tex, dev, epochs, precision, window=3):
 def oracle_sample(nnz_sample):
     """A bounded sample of the workload for the CPU oracle: the same recipe
     drawn at nnz_sample coordinates on the host, planted values by the oracle."""
-    import numpy as np
     import oracle
     w = synth.WORKLOADS[WORKLOAD]
     d = synth.draw_workload(w, device="cpu", nnz=nnz_sample)
@@ -700,39 +720,64 @@ def oracle_sample(nnz_sample):
     vals = synth.to_ratings(torch.from_numpy(pred))
     tr = d.train
     idx = np.ascontiguousarray(d.idx[:, tr].numpy())
-    x = vals[tr].double().numpy()
-    A, B = synth.initial_factors(w, mean_value=float(x.mean()))
+    _, xc = synth.centre(vals[tr])
+    x = xc.double().numpy()
+    A, B = synth.initial_factors(w)
     return w, idx, x, [a.double().numpy() for a in A], [b.double().numpy() for b in B]
 
 
-def time_oracle_step(idx, x, A, B):
+def time_oracle_step(idx, x, A, B, threads):
+    """One step of the FP64 oracle on the host: the factor epoch as Hogwild on
+    `threads` cores (each thread a contiguous range of the nonzeros, S = 1)
+    and the core epoch (Algorithm 5, the sum split over the same threads)."""
+    import oracle
+    t = time.perf_counter()
+    A = oracle.factor_epoch_hogwild(A, B, idx, x, LR, LAM, nthreads=threads)
+    B = oracle.core_epoch(A, B, idx, x, LR_B, LAM, nthreads=threads)
+    return time.perf_counter() - t, A, B
+
+
+def time_oracle_sequential(idx, x, A, B):
+    """The sequential oracle (factor epoch S = 1, one thread) on the same
+    nonzeros: the single-core figure, for context."""
     import oracle
     t = time.perf_counter()
     A = oracle.factor_epoch(A, B, idx, x, 1, LR, LAM)
     B = oracle.core_epoch(A, B, idx, x, LR_B, LAM, nthreads=1)
-    return time.perf_counter() - t, A, B
+    return time.perf_counter() - t
 
 
-def cpu_baseline(nnz_sample):
+def cpu_baseline(nnz_sample, seq_sample=1_000_000):
+    """The FP64 oracle on every host core over a bounded draw of the same
+    recipe; its rate (nonzeros per second) is taken as the full workload's,
+    since both phases are linear in the nonzeros."""
+    import oracle
     w, idx, x, A, B = oracle_sample(nnz_sample)
-    dt, _, _ = time_oracle_step(idx, x, A, B)
+    threads = oracle.default_threads()
+    dt, _, _ = time_oracle_step(idx, x, A, B, threads)
     n = int(x.shape[0])
-    return {"value": n / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{n} training nonzeros of the same recipe drawn at {nnz_sample} coordinates; "
-                      f"one sequential FP64 factor epoch (S=1) + core epoch, single thread, "
-                      f"{dt:.1f} s"}
+    k = min(n, seq_sample)
+    dt1 = time_oracle_sequential(np.ascontiguousarray(idx[:, :k]), x[:k], A, B)
+    return {"value": n / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": f"{n} training nonzeros of the same recipe drawn at {nnz_sample} coordinates "
+                      f"(rate extrapolated linearly to the full workload); one FP64 step: Hogwild factor "
+                      f"epoch + core epoch on {threads} host threads, {dt:.2f} s",
+            "sequential_1_thread": {"value": k / dt1, "unit": UNIT, "nnz": k,
+                                    "what": "sequential factor epoch (S=1) + core epoch, one thread"}}
 
 
 def run_reference(args, rank, world):
+    import oracle
     if rank != 0:
         return None
     w, idx, x, A, B = oracle_sample(args.ref_sample)
+    threads = oracle.default_threads()
     n = int(x.shape[0])
     for _ in range(args.warmup):
-        _, A, B = time_oracle_step(idx, x, A, B)
+        _, A, B = time_oracle_step(idx, x, A, B, threads)
     ts = []
     for _ in range(args.steps):
-        dt, A, B = time_oracle_step(idx, x, A, B)
+        dt, A, B = time_oracle_step(idx, x, A, B, threads)
         ts.append(dt)
     tot = sum(ts)
     value = n * len(ts) / tot
@@ -740,12 +785,13 @@ def run_reference(args, rank, world):
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / len(ts),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic (seeded Zipf coordinates, planted-model ratings; Netflix-shaped)",
+        "data": "synthetic (seeded Zipf coordinates, planted-model ratings, centred; Netflix-shaped)",
         "config": {"workload": WORKLOAD, "N": w.N, "I": list(w.I), "J": list(w.J), "R": w.R,
-                   "nnz_train_sample": n, "precision": "fp64", "scatter": "sequential"},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                   "nnz_train_sample": n, "precision": "fp64", "scatter": "hogwild (host threads)"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
                          "sample": f"{n} training nonzeros per step (same recipe at {args.ref_sample} "
-                                   f"coordinates), sequential FP64 factor + core epoch, 1 thread"},
+                                   f"coordinates); FP64 Hogwild factor epoch + core epoch on {threads} "
+                                   f"host threads; rate extrapolated linearly to the full workload"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
 
@@ -756,9 +802,11 @@ def main():
     ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--precision", choices=["fp32", "tf32", "bf16"], default="bf16")
-    ap.add_argument("--cpu-sample", type=int, default=2_000_000)
-    ap.add_argument("--ref-sample", type=int, default=1_000_000)
+    ap.add_argument("--precision", choices=["fp32", "tf32", "bf16"], default=None,
+                    help="contraction precision (default: bf16; fp32 for the batched workload, "
+                         "whose configuration is FP32)")
+    ap.add_argument("--cpu-sample", type=int, default=10_000_000)
+    ap.add_argument("--ref-sample", type=int, default=4_000_000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-time-to-rmse", action="store_true")
     ap.add_argument("--ttr-epochs", type=int, default=20,
@@ -787,6 +835,8 @@ def main():
                          "a smaller case of the same recipe, e.g. for profiling")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
+    if args.precision is None:
+        args.precision = "fp32" if args.workload == BATCHED else "bf16"
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

@@ -300,6 +300,7 @@ def mlp_nparams() -> int:
 
 
 def mlp_forward(params, X) -> np.ndarray:
+    """Multipliers exp(clamp(u, log 1/16, log 16)) of every row of features."""
     P = np.ascontiguousarray(params, dtype=np.float64)
     Xv = np.ascontiguousarray(X, dtype=np.float64).reshape(-1, 3)
     out = np.empty(Xv.shape[0])
@@ -308,7 +309,8 @@ def mlp_forward(params, X) -> np.ndarray:
 
 
 def mlp_grad(params, X, y):
-    """(gradient of mean 1/2 (s - y)^2 w.r.t. the parameters, loss)."""
+    """(gradient of mean 1/2 (u - y)^2 w.r.t. the parameters, loss): u the
+    network's linear output (log-multiplier), y log-multiplier labels."""
     P = np.ascontiguousarray(params, dtype=np.float64)
     Xv = np.ascontiguousarray(X, dtype=np.float64).reshape(-1, 3)
     yv = np.ascontiguousarray(y, dtype=np.float64)

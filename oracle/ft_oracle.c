@@ -477,9 +477,13 @@ int orc_objective(int N, const int64_t *I, const int *J, int R, double *const *A
  *   F_r(a) = sum_m [1/2 (x_m - a.p_m)^2 + 1/2 lambda |a|^2]
  * along -g_r:  t* = |g|^2 / (sum_m (p_m.g)^2 + lambda count |g|^2), expressed
  * as a multiplier of the epoch's SGD step gamma * g:  s* = t* / gamma, clipped
- * to [1/4, 4]; rows without nonzeros (or with g = 0) get s* = 1.
+ * to [1/16, 16]; the label is log s* (rows without nonzeros, or with g = 0,
+ * get log 1 = 0).
  * Rows of all modes are concatenated (mode 0 first).
  * ====================================================================== */
+#define ORC_SMIN (1.0 / 16.0)
+#define ORC_SMAX 16.0
+
 int orc_row_stats(int N, const int64_t *I, const int *J, int R, double *const *A,
                   double *const *B, int64_t nnz, const int32_t *const *idx, const double *x,
                   double lambda, double gamma, double beta, const double *ema_in,
@@ -556,10 +560,10 @@ int orc_row_stats(int N, const int64_t *I, const int *J, int R, double *const *A
         double den = hsum[q] + lambda * k * gg;
         if (k > 0.0 && gg > 0.0 && den > 0.0) {
           s = gg / den / gamma;
-          if (s < 0.25) s = 0.25;
-          if (s > 4.0) s = 4.0;
+          if (s < ORC_SMIN) s = ORC_SMIN;
+          if (s > ORC_SMAX) s = ORC_SMAX;
         }
-        label[q] = s;
+        label[q] = log(s);
       }
     }
 done:
@@ -568,8 +572,9 @@ done:
 }
 
 /*
- * Step-size network: features (3) -> 64 -> 64 -> 1 with ReLU, output
- * s = 1/4 + 15/4 sigmoid(z) in (1/4, 4).  Parameters, in this order:
+ * Step-size network: features (3) -> 64 -> 64 -> 1 with ReLU and a linear
+ * output u, the predicted log-multiplier; the multiplier is
+ * s = exp(min(max(u, log 1/16), log 16)).  Parameters, in this order:
  * W1 [64][3], b1 [64], W2 [64][64], b2 [64], w3 [64], b3 [1]  (4481 values).
  */
 #define ORC_H 64
@@ -577,7 +582,8 @@ done:
 
 int orc_mlp_nparams(void) { return ORC_NPARAM; }
 
-static double orc_mlp_row(const double *P, const double *x, double *h1, double *h2, double *zout) {
+/* The network's output u (the log-multiplier) for one row of features. */
+static double orc_mlp_row(const double *P, const double *x, double *h1, double *h2) {
   const double *W1 = P, *b1 = W1 + ORC_H * 3, *W2 = b1 + ORC_H, *b2 = W2 + ORC_H * ORC_H;
   const double *w3 = b2 + ORC_H, *b3 = w3 + ORC_H;
   for (int i = 0; i < ORC_H; ++i) {
@@ -585,39 +591,45 @@ static double orc_mlp_row(const double *P, const double *x, double *h1, double *
     for (int k = 0; k < 3; ++k) s += W1[i * 3 + k] * x[k];
     h1[i] = s > 0.0 ? s : 0.0;
   }
-  double z = b3[0];
+  double u = b3[0];
   for (int i = 0; i < ORC_H; ++i) {
     double s = b2[i];
     for (int j = 0; j < ORC_H; ++j) s += W2[i * ORC_H + j] * h1[j];
     h2[i] = s > 0.0 ? s : 0.0;
-    z += w3[i] * h2[i];
+    u += w3[i] * h2[i];
   }
-  *zout = z;
-  return 0.25 + 3.75 / (1.0 + exp(-z));
+  return u;
 }
 
+/* Multipliers s = exp(clamp(u, log 1/16, log 16)) of n rows. */
 int orc_mlp_forward(const double *P, int64_t n, const double *X, double *s) {
-  double h1[ORC_H], h2[ORC_H], z;
-  for (int64_t m = 0; m < n; ++m) s[m] = orc_mlp_row(P, X + 3 * m, h1, h2, &z);
+  double h1[ORC_H], h2[ORC_H];
+  for (int64_t m = 0; m < n; ++m) {
+    double u = orc_mlp_row(P, X + 3 * m, h1, h2);
+    if (u < log(ORC_SMIN)) u = log(ORC_SMIN);
+    if (u > log(ORC_SMAX)) u = log(ORC_SMAX);
+    s[m] = exp(u);
+  }
   return ORC_OK;
 }
 
-/* Gradient of L = (1/n) sum_m 1/2 (s_m - y_m)^2 with respect to every
- * parameter (same layout); *loss receives L. */
+/* Gradient of L = (1/n) sum_m 1/2 (u_m - y_m)^2, u the linear output and y
+ * the log-multiplier labels, with respect to every parameter (same layout);
+ * *loss receives L.  The output is not clamped in the loss, so its gradient
+ * never vanishes. */
 int orc_mlp_grad(const double *P, int64_t n, const double *X, const double *y, double *G,
                  double *loss) {
   const double *W2 = P + ORC_H * 3 + ORC_H, *w3 = W2 + ORC_H * ORC_H + ORC_H;
   double *gW1 = G, *gb1 = gW1 + ORC_H * 3, *gW2 = gb1 + ORC_H, *gb2 = gW2 + ORC_H * ORC_H;
   double *gw3 = gb2 + ORC_H, *gb3 = gw3 + ORC_H;
-  double h1[ORC_H], h2[ORC_H], dh1[ORC_H], z, L = 0.0;
+  double h1[ORC_H], h2[ORC_H], dh1[ORC_H], L = 0.0;
   for (int q = 0; q < ORC_NPARAM; ++q) G[q] = 0.0;
   for (int64_t m = 0; m < n; ++m) {
     const double *x = X + 3 * m;
-    double s = orc_mlp_row(P, x, h1, h2, &z);
-    double sg = 1.0 / (1.0 + exp(-z));
-    double r = s - y[m];
+    double u = orc_mlp_row(P, x, h1, h2);
+    double r = u - y[m];
     L += 0.5 * r * r;
-    double dz = r * 3.75 * sg * (1.0 - sg) / (double)n;
+    double dz = r / (double)n;
     gb3[0] += dz;
     for (int j = 0; j < ORC_H; ++j) dh1[j] = 0.0;
     for (int i = 0; i < ORC_H; ++i) {

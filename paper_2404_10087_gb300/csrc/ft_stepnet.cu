@@ -60,7 +60,6 @@ __global__ void k_net_init(void *net, uint64_t seed) {
     if (q < OFF_B1) w = (2.f * u - 1.f) * sqrtf(6.f / 3.f);
     else if (q >= OFF_W2 && q < OFF_B2) w = (2.f * u - 1.f) * sqrtf(6.f / H);
     else if (q >= OFF_W3 && q < OFF_B3) w = (2.f * u - 1.f) * sqrtf(6.f / H);
-    else if (q == OFF_B3) w = logf(0.25f);   // s = 1/4 + 15/4 sigmoid(log 1/4) = 1
     if (q >= NP) w = 0.f;
     nv.master[q] = w;
     nv.m[q] = nv.v[q] = nv.grad[q] = nv.last[q] = 0.f;
@@ -77,7 +76,9 @@ __device__ inline void load_weights(const NetView &nv, float *W) {
   __syncthreads();
 }
 
-__device__ inline float net_output(float z) { return 0.25f + 3.75f / (1.f + __expf(-z)); }
+// Multiplier of the linear output u (a log-multiplier), clamped to [1/16, 16].
+constexpr float kLogSMax = 2.772588722239781f;   // log 16
+__device__ inline float net_output(float u) { return expf(fminf(fmaxf(u, -kLogSMax), kLogSMax)); }
 
 __global__ void __launch_bounds__(128) k_net_forward(const NetView nv, int64_t rows, const float *feat,
                                                       float *scale) {
@@ -103,7 +104,8 @@ __global__ void __launch_bounds__(128) k_net_forward(const NetView nv, int64_t r
   }
 }
 
-// Gradient of (1/rows) sum 1/2 (s - y)^2.  One warp per block; each chunk of
+// Gradient of (1/rows) sum 1/2 (u - y)^2 (u the linear output, y the
+// log-multiplier label).  One warp per block; each chunk of
 // 32 rows (one per lane) leaves its activations in shared memory, then lane l
 // accumulates the gradient of columns l and l + 32 over the chunk (lane-private
 // shared-memory accumulators for W2), and at the end every lane adds its
@@ -153,11 +155,9 @@ __global__ void __launch_bounds__(32) k_net_backward(const NetView nv, int64_t r
       S.H2[l * LDH + i] = h2;
       z = fmaf(S.W[OFF_W3 + i], h2, z);
     }
-    const float sg = 1.f / (1.f + __expf(-z));
-    const float out = 0.25f + 3.75f * sg;
-    const float res = valid ? out - label[r] : 0.f;
+    const float res = valid ? z - label[r] : 0.f;
     loss += 0.5 * double(res) * double(res);
-    const float dz = valid ? res * 3.75f * sg * (1.f - sg) * inv_n : 0.f;
+    const float dz = res * inv_n;
     S.DZ[l] = dz;
     for (int i = 0; i < H; ++i) {
       const float dh2 = S.H2[l * LDH + i] > 0.f ? dz * S.W[OFF_W3 + i] : 0.f;

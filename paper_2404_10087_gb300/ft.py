@@ -28,6 +28,7 @@ FT_CORE_CALC, FT_CORE_STORE = 0, 1
 CORE_SCHEMES = {"calc": FT_CORE_CALC, "store": FT_CORE_STORE}
 
 FT_OK = 0
+FT_ERR_NONFINITE = -5
 STATUS = {0: "FT_OK", -1: "FT_ERR_ARG", -2: "FT_ERR_INDEX", -3: "FT_ERR_SHAPE", -4: "FT_ERR_CUDA",
           -5: "FT_ERR_NONFINITE", -6: "FT_ERR_TIMEOUT", -7: "FT_ERR_WORKSPACE"}
 

@@ -3,11 +3,12 @@ labels, step-size network) against independent computations:
 
 * counts by np.bincount, residuals and row gradients by central finite
   differences of the row's subproblem loss through the dense Tucker model;
-* the label is the exact minimiser along -g of that (quadratic) subproblem,
-  recovered from three loss evaluations;
+* the label is the log of the exact minimiser along -g of that (quadratic)
+  subproblem, recovered from three loss evaluations, over the step size;
 * the network's forward pass equals the textbook MLP written with numpy
-  matrix products, and its gradient equals central finite differences of the
-  oracle's own forward loss.
+  matrix products (linear output u, multiplier exp(clamp(u))), and its
+  gradient equals central finite differences of mean 1/2 (u - y)^2 computed
+  through that numpy network.
 """
 import numpy as np
 
@@ -35,7 +36,8 @@ def test_row_stats_against_definitions():
     ema_in = rng.uniform(0, 1, sum(I))
     feat, lab = oracle.row_stats(A, B, idx, x, lam, gamma, beta, ema_in)
     # most labels inside the clip range, so the formula itself is exercised
-    assert np.mean((lab > 0.25) & (lab < 4.0)) > 0.8
+    lo, hi = np.log(1 / 16), np.log(16)
+    assert np.mean((lab > lo) & (lab < hi)) > 0.8
     xhat = np.array([dense_predict(A, B, idx[:, m]) for m in range(len(x))])
     e = x - xhat
     off = 0
@@ -59,19 +61,20 @@ def test_row_stats_against_definitions():
             assert np.isclose(feat[q, 1], np.log1p(ema), rtol=1e-6, atol=1e-9)
             # exact line search along -g from three loss values (F is quadratic in t)
             if cnt[r] == 0 or np.linalg.norm(g) < 1e-12:
-                assert lab[q] == 1.0
+                assert lab[q] == 0.0
                 continue
             dlt = 1e-3
             f0 = row_loss(A, B, idx, x, lam, n, r, A[n][r])
             fp = row_loss(A, B, idx, x, lam, n, r, A[n][r] - dlt * g)
             fm = row_loss(A, B, idx, x, lam, n, r, A[n][r] + dlt * g)
             t_star = dlt * (fm - fp) / (2 * (fp - 2 * f0 + fm))
-            want = float(np.clip(t_star / gamma, 0.25, 4.0))
-            assert np.isclose(lab[q], want, rtol=1e-5), (n, r, lab[q], want)
+            want = float(np.log(np.clip(t_star / gamma, 1 / 16, 16)))
+            assert np.isclose(lab[q], want, rtol=1e-5, atol=1e-6), (n, r, lab[q], want)
         off += I[n]
 
 
-def mlp_numpy(P, X):
+def mlp_numpy_raw(P, X):
+    """The textbook 3 -> 64 -> 64 -> 1 ReLU network with a linear output."""
     H = 64
     W1 = P[:H * 3].reshape(H, 3)
     b1 = P[H * 3:H * 4]
@@ -81,15 +84,18 @@ def mlp_numpy(P, X):
     b3 = P[H * 6 + H * H]
     h1 = np.maximum(0.0, X @ W1.T + b1)
     h2 = np.maximum(0.0, h1 @ W2.T + b2)
-    z = h2 @ w3 + b3
-    return 0.25 + 3.75 / (1.0 + np.exp(-z))
+    return h2 @ w3 + b3
 
 
 def test_mlp_forward_is_the_textbook_network():
     rng = np.random.default_rng(4)
     P = rng.normal(0, 0.3, oracle.mlp_nparams())
     X = rng.normal(0, 1, (50, 3))
-    np.testing.assert_allclose(oracle.mlp_forward(P, X), mlp_numpy(P, X), rtol=1e-12)
+    u = mlp_numpy_raw(P, X)
+    # both sides of the clamp are exercised
+    assert np.any(np.abs(u) < np.log(16)) and np.any(np.abs(u) > np.log(16))
+    want = np.exp(np.clip(u, np.log(1 / 16), np.log(16)))
+    np.testing.assert_allclose(oracle.mlp_forward(P, X), want, rtol=1e-12)
 
 
 def test_mlp_gradient_by_central_differences():
@@ -97,9 +103,13 @@ def test_mlp_gradient_by_central_differences():
     n_par = oracle.mlp_nparams()
     P = rng.normal(0, 0.3, n_par)
     X = rng.normal(0, 1, (20, 3))
-    y = rng.uniform(0.25, 4, 20)
-    G, loss = oracle.mlp_grad(P, X, y)
-    assert np.isclose(loss, np.mean(0.5 * (oracle.mlp_forward(P, X) - y) ** 2), rtol=1e-12)
+    y = rng.uniform(np.log(1 / 16), np.log(16), 20)
+
+    def loss(Pv):
+        return float(np.mean(0.5 * (mlp_numpy_raw(Pv, X) - y) ** 2))
+
+    G, L = oracle.mlp_grad(P, X, y)
+    assert np.isclose(L, loss(P), rtol=1e-12)
     h = 1e-6
     pick = np.concatenate([np.arange(0, 192, 17), np.arange(192, 256, 7), np.arange(256, 4352, 97),
                            np.arange(4352, 4481, 11), [4480]])
@@ -107,7 +117,7 @@ def test_mlp_gradient_by_central_differences():
         Pp, Pm = P.copy(), P.copy()
         Pp[q] += h
         Pm[q] -= h
-        fd = (oracle.mlp_grad(Pp, X, y)[1] - oracle.mlp_grad(Pm, X, y)[1]) / (2 * h)
+        fd = (loss(Pp) - loss(Pm)) / (2 * h)
         assert np.isclose(G[q], fd, rtol=1e-5, atol=1e-9), q
 
 
@@ -116,7 +126,8 @@ STEPNET_PINS = [test_row_stats_against_definitions, test_mlp_forward_is_the_text
 STEPNET_MUTANTS = [
     ("label_without_regulariser_curvature", "double den = hsum[q] + lambda * k * gg;", "double den = hsum[q];"),
     ("relu_derivative_dropped", "double dh2 = h2[i] > 0.0 ? dz * w3[i] : 0.0;", "double dh2 = dz * w3[i];"),
-    ("output_range_wrong", "return 0.25 + 3.75 / (1.0 + exp(-z));", "return 0.25 + 4.0 / (1.0 + exp(-z));"),
+    ("output_clamp_wrong", "if (u > log(ORC_SMAX)) u = log(ORC_SMAX);", "if (u > log(4.0)) u = log(4.0);"),
+    ("loss_gradient_halved", "double dz = r / (double)n;", "double dz = 0.5 * r / (double)n;"),
     ("row_gradient_sign", "g[goff[n] + row * J[n] + j] += -e * pj + lambda * a[j];",
      "g[goff[n] + row * J[n] + j] += e * pj + lambda * a[j];"),
     ("mean_residual_not_divided", "feat[3 * q + 2] = k > 0.0 ? esum[q] / k : 0.0;", "feat[3 * q + 2] = esum[q];"),
