@@ -456,7 +456,8 @@ ft_status make_plan(int N, const int64_t *I, const int *J, int R, int64_t nnz, c
     if (occ_t < 1 || occ_max * p->ks.factor_tc_tmem_cols > 512) return FT_ERR_CUDA;
     p->grid_factor_tc = p->num_sms * per_sm;
   }
-  const int occ_f = occupancy(p->ks.factor, 256, tc ? p->ks.factor_smem : p->factor_smem);
+  const int occ_f = std::min(occupancy(p->ks.factor, 256, tc ? p->ks.factor_smem : p->factor_smem),
+                             occupancy(p->ks.factor_fast, 256, tc ? p->ks.factor_smem : p->factor_smem));
   const int occ_d = occupancy(p->ks.factor_delta, 256, p->ks.factor_smem);
   const bool store = c.core_scheme == FT_CORE_STORE;
   p->core_fn = store ? p->ks.core_store : p->ks.core;
@@ -919,8 +920,11 @@ ft_status ft_epoch_factors(ft_ctx *c, float lr_a, float lambda_a, const float *c
     if (p.cfg.engine == FT_ENGINE_TCGEN05)
       return launch(c, p.ks.factor_tc, p.grid_factor_tc, p.ks.factor_tc_threads,
                     c->hot_active ? p.factor_smem : p.ks.factor_tc_smem, &a, st);
-    return launch(c, p.ks.factor, p.grid_factor, 256, c->hot_active ? p.factor_smem : p.ks.factor_smem,
-                  &a, st);
+    bool scaled = false;
+    for (int n = 0; n < p.N; ++n) scaled = scaled || a.scale[n] != nullptr;
+    const bool fast = c->hot_active && !scaled && c->vecmask == (1u << p.N) - 1u;
+    return launch(c, fast ? p.ks.factor_fast : p.ks.factor, p.grid_factor, 256,
+                  c->hot_active ? p.factor_smem : p.ks.factor_smem, &a, st);
   }
 
   a.delta = ws_ptr<float>(c, p.off_delta);

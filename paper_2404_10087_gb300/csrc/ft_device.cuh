@@ -540,16 +540,21 @@ struct Front {
   }
 
   __device__ __forceinline__ void predict() {
-    // xhat = sum_r prod_n c^(n)_r: lane partial over its chunk, then the group of four
+    // xhat = sum_r prod_n c^(n)_r: lane partial over its chunk (the last
+    // factor of each product fused into the sum), then the group of four
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
       float s = 0.f;
 #pragma unroll
       for (int q = 0; q < CPL; ++q) {
-        float pr = c[0][h][q];
+        if constexpr (N == 1) {
+          s += c[0][h][q];
+        } else {
+          float pr = c[0][h][q];
 #pragma unroll
-        for (int n = 1; n < N; ++n) pr *= c[n][h][q];
-        s += pr;
+          for (int n = 1; n + 1 < N; ++n) pr *= c[n][h][q];
+          s = fmaf(pr, c[N - 1][h][q], s);
+        }
       }
       s += __shfl_xor_sync(FULL, s, 1);
       s += __shfl_xor_sync(FULL, s, 2);
@@ -722,6 +727,91 @@ __device__ __forceinline__ void factor_tile(const EpochArgs &p, const float *tab
   }
 }
 
+// The Hogwild tile of factor_tile for the common case - every mode's rows
+// exactly K wide with a 16-byte aligned base (so every chunk is one 16-byte
+// access), the hot-row cache on, one step size for every row - with the same
+// rule and no data-dependent branches: a masked nonzero (past the end, or with
+// a coordinate outside its range) reads row 0 of global memory, uses zeros,
+// and skips its stores by predication.  The update is written
+//   a <- (1 - lr lam) a + (lr e) P,
+// the same step as a + lr (e P - lam a) up to rounding.
+template <int N, int K, int MATH>
+__device__ __forceinline__ void factor_tile_fast(const EpochArgs &p, const float *tabs, float *rep,
+                                                 unsigned char *dirty, const TileCoords<N> &tc, int lane) {
+  constexpr int CPL = K / 4;
+  constexpr int TW = Prod<K, MATH>::WORDS;
+  const int t = lane & 3;
+  Front<N, K, MATH, false> f;
+  uint32_t r[N][2];      // global row, or cache slot when hot
+  bool hot[N][2];
+  bool bad = false;
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    bool ok = true;
+#pragma unroll
+    for (int n = 0; n < N; ++n) {
+      const int32_t v = tc.row[n][h];
+      const bool is_hot = v < 0;
+      const uint32_t slot = ~uint32_t(v);   // -v - 1 for a negative v
+      const bool in = is_hot ? slot - uint32_t(p.hot_base[n]) < uint32_t(p.hot_base[n + 1] - p.hot_base[n])
+                             : uint32_t(v) < uint32_t(p.I[n]);
+      ok = ok && in;
+      hot[n][h] = is_hot;
+      r[n][h] = is_hot ? slot : uint32_t(v);
+    }
+    bad = bad || (tc.valid[h] && !ok);
+    f.valid[h] = tc.valid[h] && ok;
+    f.x[h] = f.valid[h] ? tc.x[h] : 0.f;
+#pragma unroll
+    for (int n = 0; n < N; ++n) {
+      hot[n][h] = hot[n][h] && f.valid[h];
+      r[n][h] = f.valid[h] ? r[n][h] : 0u;
+    }
+  }
+  if (__any_sync(FULL, bad) && lane == 0) atomicOr(p.err, ERRBIT_INDEX);
+  // gather: one generic 16-byte access per chunk, from the cache or from
+  // global memory (masked rows read row 0 and use zeros)
+#pragma unroll
+  for (int n = 0; n < N; ++n)
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const float *src = hot[n][h] ? rep + r[n][h] * K + CPL * t : p.A[n] + size_t(r[n][h]) * K + CPL * t;
+#pragma unroll
+      for (int w = 0; w < CPL; w += 4) {
+        const float4 f4 = *reinterpret_cast<const float4 *>(src + w);
+        f.a[n][h][w] = f.valid[h] ? f4.x : 0.f;
+        f.a[n][h][w + 1] = f.valid[h] ? f4.y : 0.f;
+        f.a[n][h][w + 2] = f.valid[h] ? f4.z : 0.f;
+        f.a[n][h][w + 3] = f.valid[h] ? f4.w : 0.f;
+      }
+    }
+  f.compute(tabs, TW, lane);
+  const float e[2] = {f.x[0] - f.xhat[0], f.x[1] - f.xhat[1]};
+  const bool nonfinite = (f.valid[0] && !isfinite(e[0])) || (f.valid[1] && !isfinite(e[1]));
+  if (__any_sync(FULL, nonfinite) && lane == 0) atomicOr(p.err, ERRBIT_NONFINITE);
+  const float keep = 1.f - p.lr * p.lam;
+  const float ge[2] = {p.lr * e[0], p.lr * e[1]};
+#pragma unroll
+  for (int n = 0; n < N; ++n) {
+    float d[2][CPL], pp[2][CPL];
+    f.leave_one_out(n, d);
+    Prod<K, MATH>::run(d, tabs + (N + n) * TW, pp, lane);
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      float *dst = hot[n][h] ? rep + r[n][h] * K + CPL * t : p.A[n] + size_t(r[n][h]) * K + CPL * t;
+#pragma unroll
+      for (int w = 0; w < CPL; w += 4) {
+        const float4 o = make_float4(fmaf(ge[h], pp[h][w], keep * f.a[n][h][w]),
+                                     fmaf(ge[h], pp[h][w + 1], keep * f.a[n][h][w + 1]),
+                                     fmaf(ge[h], pp[h][w + 2], keep * f.a[n][h][w + 2]),
+                                     fmaf(ge[h], pp[h][w + 3], keep * f.a[n][h][w + 3]));
+        if (f.valid[h]) *reinterpret_cast<float4 *>(dst + w) = o;
+      }
+      if (hot[n][h] && t == 0) dirty[r[n][h]] = 1;
+    }
+  }
+}
+
 // ------------------------------------------------------------- factor phase
 // One pass of the factor update over [begin, end) (Algorithm 4).
 //
@@ -742,7 +832,9 @@ __device__ __forceinline__ void factor_tile(const EpochArgs &p, const float *tab
 //
 // DELTA = true: the per-nonzero step is written to p.delta for the
 // deterministic batch reduction; A is not modified.
-template <int N, int K, int MATH, bool DELTA>
+// FAST (Hogwild with the hot-row cache, every mode full width, one step size
+// for every row): the tiles run factor_tile_fast.
+template <int N, int K, int MATH, bool DELTA, bool FAST = false>
 __global__ void __launch_bounds__(256) k_factor(const EpochArgs p) {
   extern __shared__ __align__(16) float smem[];
   using L = FactorSmem<N, K, MATH>;
@@ -785,7 +877,10 @@ __global__ void __launch_bounds__(256) k_factor(const EpochArgs p) {
   for (int64_t c = blockIdx.x; c < nct; c += G) {
     const int64_t cn = c + G;
     if (cn < nct) nxt.load(p, p.begin + (cn * wpc + wid) * FT_TILE, lane, true);
-    if (c * wpc + wid < ntiles) factor_tile<N, K, MATH, false>(p, smem, rep, dirty, cur, lane);
+    if (c * wpc + wid < ntiles) {
+      if constexpr (FAST) factor_tile_fast<N, K, MATH>(p, smem, rep, dirty, cur, lane);
+      else factor_tile<N, K, MATH, false>(p, smem, rep, dirty, cur, lane);
+    }
     cur = nxt;
     if (++k == W || cn >= nct) {
       k = 0;

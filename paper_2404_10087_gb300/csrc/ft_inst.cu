@@ -35,6 +35,7 @@ template <int N>
 ft::KernelSet make_set() {
   ft::KernelSet s;
   s.factor = reinterpret_cast<const void *>(&ft::k_factor<N, FT_K, FT_MATH, false>);
+  s.factor_fast = reinterpret_cast<const void *>(&ft::k_factor<N, FT_K, FT_MATH, false, true>);
   s.factor_delta = reinterpret_cast<const void *>(&ft::k_factor<N, FT_K, FT_MATH, true>);
   s.core = reinterpret_cast<const void *>(&ft::k_core<N, FT_K, FT_KMATH>);
   s.factor_smem = ft::FactorSmem<N, FT_K, FT_MATH>::tables();

@@ -86,7 +86,7 @@ def test_batched_core_steps_and_errors(recipe):
 
 def test_batched_hogwild_epoch_properties(recipe):
     b, tensors = make_batch(recipe)
-    b.epoch(0.01, LAM, LR_B, LAM)   # the benchmark's steps
+    b.epoch(0.005, LAM, LR_B, LAM)   # the benchmark's steps
     torch.cuda.synchronize()
     sse_before = sse_after = 0.0
     for k, (t, (gi, gx, gA, gB)) in enumerate(zip(recipe, tensors)):
