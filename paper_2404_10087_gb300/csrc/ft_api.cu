@@ -433,25 +433,33 @@ ft_status make_plan(int N, const int64_t *I, const int *J, int R, int64_t nnz, c
   if (tc && (K != 16 || p->ks.factor_tc == nullptr)) return FT_ERR_ARG;
   const size_t factor_base_smem = tc ? p->ks.factor_tc_smem : p->ks.factor_smem;
   p->hot_cap = 0;
+  // The tcgen05 pass with every row full width stages the next tile's rows
+  // in shared memory after the cache (4 warpgroups x N x 128 rows of 64 B);
+  // the default cache takes what is left.
+  bool full_width = true;
+  for (int n = 0; n < N; ++n) full_width = full_width && J[n] == K;
+  size_t stage_bytes = 0;
   if (c.scatter == FT_HOGWILD && c.hot_rows != 0 && nnz > 0) {
+    if (tc && full_width) stage_bytes = size_t(4) * N * 128 * 64;
     const size_t per_slot = size_t(K) * sizeof(float) + 1;
     int64_t sumI = 0;
     for (int n = 0; n < N; ++n) sumI += I[n];
-    int64_t cap = c.hot_rows > 0 ? c.hot_rows : int64_t(kHotCacheBytes / per_slot);
+    const int64_t fit = int64_t((kMaxSmem - factor_base_smem - stage_bytes - 64) / per_slot);
+    int64_t cap = c.hot_rows > 0 ? c.hot_rows : std::min<int64_t>(int64_t(kHotCacheBytes / per_slot), fit);
     cap = std::min(cap, sumI);
-    const int64_t fit = int64_t((kMaxSmem - factor_base_smem - 64) / per_slot);
     if (cap > fit) return FT_ERR_ARG;
     p->hot_cap = int(std::max<int64_t>(cap, 0));
   }
   p->factor_smem = factor_base_smem + size_t(p->hot_cap) * K * sizeof(float) +
-                   ((size_t(p->hot_cap) + 15) / 16) * 16;
+                   ((size_t(p->hot_cap) + 15) / 16) * 16 + stage_bytes;
   (void)maxI;
   if (tc) {
     // one CTA of 4 warpgroups per SM; the CTAs an SM can hold must not ask
     // for more than its 512 TMEM columns (tcgen05.alloc would wait)
     // (checked at the smallest launch, without the cache, where most fit)
     const int occ_max = occupancy(p->ks.factor_tc, p->ks.factor_tc_threads, p->ks.factor_tc_smem);
-    const int occ_t = occupancy(p->ks.factor_tc, p->ks.factor_tc_threads, p->factor_smem);
+    const int occ_t = std::min(occupancy(p->ks.factor_tc, p->ks.factor_tc_threads, p->factor_smem),
+                               occupancy(p->ks.factor_tc_async, p->ks.factor_tc_threads, p->factor_smem));
     const int per_sm = std::min(occ_t, c.blocks_per_sm ? c.blocks_per_sm : 1);
     if (occ_t < 1 || occ_max * p->ks.factor_tc_tmem_cols > 512) return FT_ERR_CUDA;
     p->grid_factor_tc = p->num_sms * per_sm;
@@ -917,12 +925,12 @@ ft_status ft_epoch_factors(ft_ctx *c, float lr_a, float lambda_a, const float *c
       a.hot_snap = ws_ptr<float>(c, p.off_snap);
       a.hot_weight = ws_ptr<float>(c, p.off_hotw);
     }
-    if (p.cfg.engine == FT_ENGINE_TCGEN05)
-      return launch(c, p.ks.factor_tc, p.grid_factor_tc, p.ks.factor_tc_threads,
-                    c->hot_active ? p.factor_smem : p.ks.factor_tc_smem, &a, st);
     bool scaled = false;
     for (int n = 0; n < p.N; ++n) scaled = scaled || a.scale[n] != nullptr;
     const bool fast = c->hot_active && !scaled && c->vecmask == (1u << p.N) - 1u;
+    if (p.cfg.engine == FT_ENGINE_TCGEN05)
+      return launch(c, fast ? p.ks.factor_tc_async : p.ks.factor_tc, p.grid_factor_tc, p.ks.factor_tc_threads,
+                    c->hot_active ? p.factor_smem : p.ks.factor_tc_smem, &a, st);
     return launch(c, fast ? p.ks.factor_fast : p.ks.factor, p.grid_factor, 256,
                   c->hot_active ? p.factor_smem : p.ks.factor_smem, &a, st);
   }

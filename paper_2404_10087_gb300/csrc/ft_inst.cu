@@ -67,6 +67,7 @@ ft::KernelSet make_set() {
 #if FT_K == 16 && FT_MATH == 2
   if constexpr (N <= 4) {
     s.factor_tc = reinterpret_cast<const void *>(&ft::k_factor_tc<N>);
+    s.factor_tc_async = reinterpret_cast<const void *>(&ft::k_factor_tc<N, true>);
     s.factor_tc_smem = ft::tc::Smem<N>::bytes(0);
     s.factor_tc_threads = ft::tc::THREADS;
     s.factor_tc_tmem_cols = ft::tc::Smem<N>::TMEM_COLS;

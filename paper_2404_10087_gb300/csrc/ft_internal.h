@@ -31,6 +31,9 @@ struct KernelSet {
   int batch_core_threads = 256;
   // tcgen05 Hogwild factor pass (BF16, K = 16, N <= 4), or null
   const void *factor_tc = nullptr;
+  // the same pass with the rows of the next tile arriving by bulk copies
+  // (hot-row cache on, every row full width, one step size)
+  const void *factor_tc_async = nullptr;
   size_t factor_tc_smem = 0;           // without the hot-row cache
   int factor_tc_threads = 0;
   int factor_tc_tmem_cols = 0;         // TMEM columns one CTA allocates

@@ -142,14 +142,17 @@ struct Smem {
   static constexpr uint32_t BT = 0;                         // B operands of C = A B (rows: r, k: j)
   static constexpr uint32_t BN = BT + N * BOPND;            // B operands of P = D B^T (rows: j, k: r)
   static constexpr uint32_t OP = (BN + N * BOPND + 1023) / 1024 * 1024;  // [WGS][N] staging tiles
-  static constexpr uint32_t BAR = OP + WGS * N * OPND;      // one mbarrier per warpgroup
-  static constexpr uint32_t TSLOT = BAR + 8 * WGS;          // TMEM base address
+  static constexpr uint32_t BAR = OP + WGS * N * OPND;      // per warpgroup: MMA mbarrier, stage mbarrier
+  static constexpr uint32_t TSLOT = BAR + 16 * WGS;         // TMEM base address
   static constexpr uint32_t HOT = (TSLOT + 16 + 15) / 16 * 16;  // hot-row cache, then dirty flags
   static constexpr uint32_t COLS_USED = WGS * 16 * N;
   static constexpr uint32_t TMEM_COLS = COLS_USED <= 32 ? 32 : COLS_USED <= 64 ? 64 : COLS_USED <= 128 ? 128 : 256;
   static constexpr size_t bytes(int hot_cap) {
     return HOT + size_t(hot_cap) * 16 * sizeof(float) + (size_t(hot_cap) + 15) / 16 * 16;
   }
+  // the asynchronous row stage of one warpgroup: [N][TM] FP32 rows of 16
+  static constexpr size_t STAGE_WG = size_t(N) * TM * 16 * sizeof(float);
+  static constexpr size_t stage_bytes() { return WGS * STAGE_WG; }
 };
 
 // Coordinates and value of the lane's own slab row (loaded a tile ahead).
@@ -366,6 +369,250 @@ __device__ __forceinline__ void tile(const EpochArgs &p, unsigned char *sm, floa
   fence_before();
 }
 
+// ---------------------------------------------------- asynchronous row stage
+// The tile's rows as the thread that owns the tile row sees them (thread
+// 32 q + lane of a warpgroup owns row 32 q + lane): per mode the global row or
+// cache slot and whether it is hot, the value and whether the nonzero is
+// valid (inside the range, every coordinate in bounds).
+template <int N>
+struct RowDec {
+  uint32_t r[N];
+  unsigned hot;        // bit n
+  bool valid;
+  float x;
+  // returns true when a valid nonzero had a coordinate out of bounds
+  __device__ __forceinline__ bool decode(const EpochArgs &p, const RowCoord<N> &rc) {
+    bool ok = true;
+    hot = 0u;
+#pragma unroll
+    for (int n = 0; n < N; ++n) {
+      const int32_t v = rc.row[n];
+      const bool is_hot = v < 0;
+      const uint32_t slot = ~uint32_t(v);
+      ok = ok && (is_hot ? slot - uint32_t(p.hot_base[n]) < uint32_t(p.hot_base[n + 1] - p.hot_base[n])
+                         : uint32_t(v) < uint32_t(p.I[n]));
+      r[n] = is_hot ? slot : uint32_t(v);
+      hot |= unsigned(is_hot) << n;
+    }
+    const bool bad = rc.valid && !ok;
+    valid = rc.valid && ok;
+    x = valid ? rc.x : 0.f;
+    if (!valid) {
+      hot = 0u;
+#pragma unroll
+      for (int n = 0; n < N; ++n) r[n] = 0u;
+    }
+    return bad;
+  }
+};
+
+// The owner of tile row `row` arrives on the warpgroup's stage mbarrier,
+// announcing the bytes it will copy, and copies each of its cold rows (64
+// bytes, 16-byte aligned: the fast path's rows are full width) into the
+// stage with one bulk copy that completes on the mbarrier.
+template <int N>
+__device__ __forceinline__ void stage_issue(const EpochArgs &p, const RowDec<N> &d, unsigned char *stage, int row,
+                                            uint32_t bar) {
+  uint32_t bytes = 0;
+#pragma unroll
+  for (int n = 0; n < N; ++n) bytes += (d.valid && !((d.hot >> n) & 1u)) ? 64u : 0u;
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+#pragma unroll
+  for (int n = 0; n < N; ++n) {
+    if (d.valid && !((d.hot >> n) & 1u)) {
+      const float *src = p.A[n] + size_t(d.r[n]) * 16;
+      const uint32_t dst = saddr(stage + (size_t(n) * TM + row) * 64);
+      asm volatile(
+          "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], 64, [%2];" ::"r"(dst),
+          "l"(src), "r"(bar)
+          : "memory");
+    }
+  }
+}
+
+// One warpgroup tile with its cold rows arriving in the stage (started one
+// tile ahead by stage_issue) and hot rows read from the cache: the same
+// arithmetic as tile(), written without data-dependent branches.  After the
+// rows have been read (and the warpgroup has synchronised) the owners of the
+// next tile's rows start its copies, so they overlap this tile's products.
+// `active`: this warpgroup has a tile here (otherwise only the stage
+// protocol runs).  Returns with every TMEM read of the tile done and fenced.
+template <int N>
+__device__ __forceinline__ void tile_async(const EpochArgs &p, unsigned char *sm, float *rep, unsigned char *dirty,
+                                           unsigned char *stage, const RowDec<N> &own, bool active,
+                                           bool has_next, RowDec<N> &own_next, const RowCoord<N> &next_rc,
+                                           uint32_t tcol, uint32_t bar, uint32_t sbar, uint32_t &phase,
+                                           uint32_t &sphase, bool &aborted) {
+  using L = Smem<N>;
+  const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+  const int w = threadIdx.x >> 5, wg = w >> 2, q = w & 3;
+  const bool issuer = (threadIdx.x & 127) == 0;
+  unsigned char *op = sm + L::OP + uint32_t(wg * N) * OPND;
+  const uint32_t tslab = tcol + (uint32_t(32 * q) << 16);
+  const uint32_t rep_s = saddr(rep != nullptr ? rep : reinterpret_cast<float *>(sm));
+  const uint32_t stage_s = saddr(stage);
+
+  // this tile's rows have arrived
+  {
+    const bool ok = __all_sync(FULL, aborted ? false : wait_parity(sbar, sphase));
+    sphase ^= 1u;
+    if (!ok && !aborted) {
+      aborted = true;
+      if (lane == 0) atomicOr(p.err, ERRBIT_TIMEOUT);
+    }
+  }
+  // the lane's rows g + 8h of its slab, from the owners g + 8h
+  uint32_t r[N][4];
+  unsigned hot = 0u;
+  float x[4];
+  bool valid[4];
+#pragma unroll
+  for (int h = 0; h < 4; ++h) {
+    const int src = g + 8 * h;
+    valid[h] = __shfl_sync(FULL, own.valid, src);
+    x[h] = __shfl_sync(FULL, own.x, src);
+    const unsigned hb = __shfl_sync(FULL, own.hot, src);
+#pragma unroll
+    for (int n = 0; n < N; ++n) {
+      r[n][h] = __shfl_sync(FULL, own.r[n], src);
+      hot |= ((hb >> n) & 1u) << (4 * n + h);
+    }
+  }
+  // gather (a2) and stage as the BF16 operand of C = A B (a3)
+  float a[N][4][4];
+#pragma unroll
+  for (int n = 0; n < N; ++n)
+#pragma unroll
+    for (int h = 0; h < 4; ++h) {
+      const bool is_hot = (hot >> (4 * n + h)) & 1u;
+      const uint32_t src = is_hot ? rep_s + (r[n][h] * 16 + 4 * t) * 4u
+                                  : stage_s + uint32_t((n * TM + 32 * q + g + 8 * h) * 16 + 4 * t) * 4u;
+      float4 f4;
+      asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];" : "=f"(f4.x), "=f"(f4.y), "=f"(f4.z), "=f"(f4.w) : "r"(src)
+                   : "memory");
+      a[n][h][0] = valid[h] ? f4.x : 0.f;
+      a[n][h][1] = valid[h] ? f4.y : 0.f;
+      a[n][h][2] = valid[h] ? f4.z : 0.f;
+      a[n][h][3] = valid[h] ? f4.w : 0.f;
+      st_op(op + n * OPND, 32 * q + g + 8 * h, 4 * t, a[n][h]);
+    }
+  fence_async_smem();
+  wg_sync(wg);
+  // every thread of the warpgroup has read the stage: start the next tile's
+  // copies (after a timeout only the arrival, so the phase still completes)
+  if (has_next) {
+    const bool bad = own_next.decode(p, next_rc);
+    if (__any_sync(FULL, bad) && lane == 0) atomicOr(p.err, ERRBIT_INDEX);
+    if (aborted) own_next.valid = false;
+    stage_issue<N>(p, own_next, stage, 32 * q + lane, sbar);
+  }
+  if (!active) return;
+  if (issuer && !aborted) {
+    fence_after();
+#pragma unroll
+    for (int n = 0; n < N; ++n)
+      mma(tcol + 16 * n, sdesc(saddr(op + n * OPND)), sdesc(saddr(sm + L::BT + n * BOPND)));
+    commit(bar);
+  }
+  {
+    const bool ok = __all_sync(FULL, aborted ? false : wait_parity(bar, phase));
+    phase ^= 1u;
+    if (!ok && !aborted) {
+      aborted = true;
+      if (lane == 0) atomicOr(p.err, ERRBIT_TIMEOUT);
+    }
+  }
+  fence_after();
+
+  // prediction and residual (Eq. "fasttucker")
+  float e[4];
+  {
+    float pr[4][4];
+#pragma unroll
+    for (int n = 0; n < N; ++n) {
+      float c[4][4];
+      if (!aborted) ld_rows(tslab + 16 * n, c);
+      else {
+#pragma unroll
+        for (int h = 0; h < 4; ++h) c[h][0] = c[h][1] = c[h][2] = c[h][3] = 0.f;
+      }
+#pragma unroll
+      for (int h = 0; h < 4; ++h)
+#pragma unroll
+        for (int k = 0; k < 4; ++k) pr[h][k] = n == 0 ? c[h][k] : pr[h][k] * c[h][k];
+    }
+    bool nf = false;
+#pragma unroll
+    for (int h = 0; h < 4; ++h) {
+      float s = (pr[h][0] + pr[h][1]) + (pr[h][2] + pr[h][3]);
+      s += __shfl_xor_sync(FULL, s, 1);
+      s += __shfl_xor_sync(FULL, s, 2);
+      e[h] = valid[h] ? x[h] - s : 0.f;
+      nf = nf || (valid[h] && !isfinite(e[h]));
+    }
+    if (__any_sync(FULL, nf) && lane == 0) atomicOr(p.err, ERRBIT_NONFINITE);
+  }
+
+  // D^(n) = *_{k != n} C^(k), staged as the A operand of P = D B^T
+#pragma unroll
+  for (int n = 0; n < N; ++n) {
+    float d[4][4];
+#pragma unroll
+    for (int h = 0; h < 4; ++h) d[h][0] = d[h][1] = d[h][2] = d[h][3] = 1.f;
+#pragma unroll
+    for (int k = 0; k < N; ++k) {
+      if (k == n || aborted) continue;
+      float c[4][4];
+      ld_rows(tslab + 16 * k, c);
+#pragma unroll
+      for (int h = 0; h < 4; ++h)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) d[h][j] *= c[h][j];
+    }
+#pragma unroll
+    for (int h = 0; h < 4; ++h) st_op(op + n * OPND, 32 * q + g + 8 * h, 4 * t, d[h]);
+  }
+  fence_async_smem();
+  fence_before();
+  wg_sync(wg);
+  if (issuer && !aborted) {
+    fence_after();
+#pragma unroll
+    for (int n = 0; n < N; ++n)
+      mma(tcol + 16 * n, sdesc(saddr(op + n * OPND)), sdesc(saddr(sm + L::BN + n * BOPND)));
+    commit(bar);
+  }
+  {
+    const bool ok = __all_sync(FULL, aborted ? false : wait_parity(bar, phase));
+    phase ^= 1u;
+    if (!ok && !aborted) {
+      aborted = true;
+      if (lane == 0) atomicOr(p.err, ERRBIT_TIMEOUT);
+    }
+  }
+  fence_after();
+
+  // a <- (1 - lr lam) a + (lr e) P, to the cache or to global memory
+  const float keep = 1.f - p.lr * p.lam;
+#pragma unroll
+  for (int n = 0; n < N; ++n) {
+    float pp[4][4];
+    if (aborted) break;
+    ld_rows(tslab + 16 * n, pp);
+#pragma unroll
+    for (int h = 0; h < 4; ++h) {
+      const bool is_hot = (hot >> (4 * n + h)) & 1u;
+      const float ge = p.lr * e[h];
+      float *dst = is_hot ? rep + size_t(r[n][h]) * 16 + 4 * t : p.A[n] + size_t(r[n][h]) * 16 + 4 * t;
+      const float4 o = make_float4(fmaf(ge, pp[h][0], keep * a[n][h][0]), fmaf(ge, pp[h][1], keep * a[n][h][1]),
+                                   fmaf(ge, pp[h][2], keep * a[n][h][2]), fmaf(ge, pp[h][3], keep * a[n][h][3]));
+      if (valid[h]) *reinterpret_cast<float4 *>(dst) = o;
+      if (valid[h] && is_hot && t == 0) dirty[r[n][h]] = 1;
+    }
+  }
+  fence_before();
+}
+
 }  // namespace tc
 
 // One Hogwild pass of the factor update over [begin, end) on tcgen05.
@@ -374,7 +621,9 @@ __device__ __forceinline__ void tile(const EpochArgs &p, unsigned char *sm, floa
 // refreshes them every max(1, hot_window / 4) CTA tiles, i.e. after the same
 // number of nonzeros per CTA as k_factor.  A timed-out MMA wait latches
 // ERRBIT_TIMEOUT; the CTA stops at its next window boundary and frees TMEM.
-template <int N>
+// ASYNC (hot-row cache on, every row full width, one step size): the rows
+// of the next tile arrive in a per-warpgroup stage by bulk copies (tile_async).
+template <int N, bool ASYNC = false>
 __global__ void __launch_bounds__(tc::THREADS, 1) k_factor_tc(const EpochArgs p) {
   using L = tc::Smem<N>;
   extern __shared__ __align__(1024) unsigned char sm[];
@@ -399,8 +648,12 @@ __global__ void __launch_bounds__(tc::THREADS, 1) k_factor_tc(const EpochArgs p)
   uint64_t *bars = reinterpret_cast<uint64_t *>(sm + L::BAR);
   uint32_t *tslot = reinterpret_cast<uint32_t *>(sm + L::TSLOT);
   if (tid == 0) {
-    for (int b = 0; b < tc::WGS; ++b)
+    for (int b = 0; b < tc::WGS; ++b) {
       asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(tc::saddr(bars + b)), "r"(1) : "memory");
+      // stage barrier: every thread of the warpgroup arrives once per tile
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(tc::saddr(bars + tc::WGS + b)), "r"(128)
+                   : "memory");
+    }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (w == 0) {
@@ -423,6 +676,50 @@ __global__ void __launch_bounds__(tc::THREADS, 1) k_factor_tc(const EpochArgs p)
   const int64_t nct = (ntiles + tc::WGS - 1) / tc::WGS;
   const int64_t G = gridDim.x;
   const int W = (cache && p.hot_window > 0) ? (p.hot_window + tc::WGS - 1) / tc::WGS : 16;
+  if constexpr (ASYNC) {
+    // the warpgroup's stage follows the dirty flags
+    unsigned char *stage = dirty + (size_t(p.hot_cap) + 15) / 16 * 16 + size_t(wg) * L::STAGE_WG;
+    const uint32_t sbar = tc::saddr(bars + tc::WGS + wg);
+    uint32_t sphase = 0;
+    auto row_of = [&](int64_t c) { return p.begin + (c * tc::WGS + wg) * tc::TM + 32 * q + lane; };
+    tc::RowCoord<N> rc;
+    tc::RowDec<N> d0, d1;
+    if (blockIdx.x < nct) {
+      rc.load(p, row_of(blockIdx.x));
+      const bool bad = d0.decode(p, rc);
+      if (__any_sync(FULL, bad) && lane == 0) atomicOr(p.err, ERRBIT_INDEX);
+      tc::stage_issue<N>(p, d0, stage, 32 * q + lane, sbar);
+    }
+    if (blockIdx.x + G < nct) rc.load(p, row_of(blockIdx.x + G));
+    int k = 0;
+    bool pending = blockIdx.x < nct;   // a stage phase was started and not waited for
+    auto step = [&](int64_t c, const tc::RowDec<N> &cur, tc::RowDec<N> &nxt) -> bool {
+      const int64_t c1 = c + G, c2 = c + 2 * G;
+      tc::tile_async<N>(p, sm, rep, dirty, stage, cur, c * tc::WGS + wg < ntiles, c1 < nct, nxt, rc, tcol, bar,
+                        sbar, phase, sphase, aborted);
+      pending = c1 < nct;
+      if (c2 < nct) rc.load(p, row_of(c2));
+      if (++k == W || c1 >= nct) {
+        k = 0;
+        const bool stop = __syncthreads_or(aborted) != 0;
+        cache_write_back<N, 16>(p, rep, dirty);
+        if (stop) return false;
+        if (c1 < nct) {
+          __syncthreads();
+          cache_refresh<N, 16>(p, rep);
+          __syncthreads();
+        }
+      }
+      return c1 < nct;
+    };
+    for (int64_t c = blockIdx.x; c < nct; c += 2 * G) {
+      if (!step(c, d0, d1)) break;
+      if (!step(c + G, d1, d0)) break;
+    }
+    // copies started for a tile that never ran (a stop after a timeout):
+    // wait for them, with a limit, before the CTA leaves
+    if (pending) (void)tc::wait_parity(sbar, sphase);
+  } else {
   tc::RowCoord<N> cur, nxt;
   if (blockIdx.x < nct) cur.load(p, p.begin + (int64_t(blockIdx.x) * tc::WGS + wg) * tc::TM + 32 * q + lane);
   int k = 0;
@@ -442,6 +739,7 @@ __global__ void __launch_bounds__(tc::THREADS, 1) k_factor_tc(const EpochArgs p)
         __syncthreads();
       }
     }
+  }
   }
   tc::fence_before();
   __syncthreads();

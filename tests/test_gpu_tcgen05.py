@@ -1,6 +1,10 @@
 """The tcgen05 factor pass (FT_ENGINE_TCGEN05: 128-nonzero warpgroup tiles,
 products on tcgen05.mma with TMEM accumulators) against the FP64 oracle,
-through the C ABI.
+through the C ABI.  With the hot-row cache on, every row full width and one
+step size (the full-width shapes below with a cache), the rows of the next
+tile arrive by bulk copies (cp.async.bulk on an mbarrier) while the current
+tile computes; the other shapes and the row-scale test run the pass that
+gathers through registers.
 
 Tolerances as for the BF16 warp-tile pass: one epoch's step A_new - A_old
 element by element within 2e-2 of the oracle's against the absolute-value
