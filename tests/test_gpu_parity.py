@@ -607,3 +607,37 @@ def test_nonfinite_residual_is_latched():
         m.check()
     assert e.value.status == -5
     m.check()  # the latch was cleared
+
+
+@pytest.mark.parametrize("precision", ["fp32", "bf16"])
+def test_fast_tile_reports_bad_coordinates_and_nonfinite(precision):
+    """The branch-free Hogwild tile (every mode full width, hot-row cache on,
+    one step size) masks a coordinate outside its range (FT_ERR_INDEX) and
+    latches a non-finite residual (FT_ERR_NONFINITE); rows of the masked
+    nonzero are not written, and the next clean epoch clears the latch."""
+    nnz = 16 * 30 + 7
+    I, J, R = (nnz + 3, nnz + 5, nnz + 1), (16, 16, 16), 16
+    g = torch.Generator().manual_seed(17)
+    idx = torch.stack([torch.randperm(In, generator=g)[:nnz] for In in I]).to(torch.int32)
+    _, x, A, B = synth.random_problem(17, I, J, R, nnz)
+    gidx, gx, gA, gB = to_dev(idx, x, A, B)
+    m = ft.FastTuckerPlus(gidx, gx, gA, gB, precision=precision, hot_min_count=1)
+    bad = [t.clone() for t in gidx]
+    bad[0][40] = I[0] + 2
+    m.rebind(bad, gx)
+    before = [a.clone() for a in gA]
+    m.epoch_factors(0.03, 0.02)
+    with pytest.raises(ft.FtError) as e:
+        m.check()
+    assert e.value.status == -2
+    for n in (1, 2):   # the masked nonzero's other rows are untouched
+        r = int(idx[n, 40])
+        assert torch.equal(gA[n][r], before[n][r])
+    m.rebind(gidx, gx)
+    m.epoch_factors(0.03, 0.02)
+    m.check()
+    gB[0][0, 0] = float("inf")
+    m.epoch_factors(0.03, 0.02)
+    with pytest.raises(ft.FtError) as e:
+        m.check()
+    assert e.value.status == -5

@@ -168,6 +168,30 @@ def test_bad_index_is_reported_and_masked():
     m.close()
 
 
+def test_bad_index_is_reported_and_masked_async():
+    """The same with the hot-row cache on and full-width rows, where the rows
+    arrive by bulk copies: the masked nonzero's rows are neither copied nor
+    written."""
+    J, R, nnz = (16, 16, 16), 16, 600
+    I, idx, x, A, B = distinct_rows_problem(16, nnz, J, R)
+    gidx = [idx[n].contiguous().to(DEV) for n in range(3)]
+    gA = [a.clone().to(DEV) for a in A]
+    m = ft.FastTuckerPlus(gidx, x.to(DEV), gA, [b.to(DEV) for b in B], precision="bf16", engine="tcgen05",
+                          hot_min_count=1)
+    bad = [t.clone() for t in gidx]
+    bad[1][17] = I[1] + 3
+    m.rebind(bad, x.to(DEV))
+    before = [a.clone() for a in gA]
+    m.epoch_factors(0.03, 0.02)
+    with pytest.raises(ft.FtError) as e:
+        m.check()
+    assert e.value.status == -2
+    for n in (0, 2):
+        r = int(idx[n, 17])
+        assert torch.equal(gA[n][r], before[n][r])
+    m.close()
+
+
 def test_empty_and_single_nonzero():
     for nnz in (0, 1):
         J, R = (16, 16, 16), 16
