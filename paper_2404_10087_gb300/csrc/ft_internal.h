@@ -31,7 +31,7 @@ struct KernelSet {
   int batch_core_threads = 256;
   // tcgen05 Hogwild factor pass (BF16, K = 16, N <= 4), or null
   const void *factor_tc = nullptr;
-  // the same pass with the rows of the next tile arriving by bulk copies
+  // the same pass with the rows of the next tile arriving by asynchronous copies
   // (hot-row cache on, every row full width, one step size)
   const void *factor_tc_async = nullptr;
   size_t factor_tc_smem = 0;           // without the hot-row cache

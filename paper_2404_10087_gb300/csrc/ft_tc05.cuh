@@ -406,28 +406,36 @@ struct RowDec {
   }
 };
 
-// The owner of tile row `row` arrives on the warpgroup's stage mbarrier,
-// announcing the bytes it will copy, and copies each of its cold rows (64
-// bytes, 16-byte aligned: the fast path's rows are full width) into the
-// stage with one bulk copy that completes on the mbarrier.
+// The warp copies the cold rows of its 32 tile rows (owned by its lanes)
+// into the stage: lane 4 g + t copies the 16-byte quarter t of rows g + 8 h,
+// h = 0..3, of every mode with cp.async (the fast path's rows are full width,
+// 64 bytes, 16-byte aligned), so each copy instruction of the warp moves eight
+// whole rows.  Each thread then arrives on the warpgroup's stage mbarrier
+// (count 128) once its own copies have landed (arrive.noinc), so the phase
+// completes when every copy of the warpgroup has.  Hot and invalid rows copy
+// nothing; a thread without copies arrives at once.
 template <int N>
-__device__ __forceinline__ void stage_issue(const EpochArgs &p, const RowDec<N> &d, unsigned char *stage, int row,
-                                            uint32_t bar) {
-  uint32_t bytes = 0;
+__device__ __forceinline__ void stage_issue(const EpochArgs &p, const RowDec<N> &d, unsigned char *stage, int q,
+                                            int lane, uint32_t bar) {
+  const int g = lane >> 2, t = lane & 3;
+  const unsigned cold = d.valid ? (~d.hot & ((1u << N) - 1u)) : 0u;
+  const uint32_t base = saddr(stage) + uint32_t((32 * q + g) * 64 + 16 * t);
 #pragma unroll
-  for (int n = 0; n < N; ++n) bytes += (d.valid && !((d.hot >> n) & 1u)) ? 64u : 0u;
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+  for (int h = 0; h < 4; ++h) {
+    const unsigned cb = __shfl_sync(FULL, cold, g + 8 * h);
 #pragma unroll
-  for (int n = 0; n < N; ++n) {
-    if (d.valid && !((d.hot >> n) & 1u)) {
-      const float *src = p.A[n] + size_t(d.r[n]) * 16;
-      const uint32_t dst = saddr(stage + (size_t(n) * TM + row) * 64);
+    for (int n = 0; n < N; ++n) {
+      const uint32_t rn = __shfl_sync(FULL, d.r[n], g + 8 * h);
+      const float *src = p.A[n] + size_t(rn) * 16 + 4 * t;
+      const uint32_t dst = base + uint32_t((n * TM + 8 * h) * 64);
       asm volatile(
-          "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], 64, [%2];" ::"r"(dst),
-          "l"(src), "r"(bar)
+          "{\n\t.reg .pred pc;\n\tsetp.ne.b32 pc, %2, 0;\n\t"
+          "@pc cp.async.cg.shared.global [%0], [%1], 16;\n\t}" ::"r"(dst),
+          "l"(src), "r"((cb >> n) & 1u)
           : "memory");
     }
   }
+  asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(bar) : "memory");
 }
 
 // One warpgroup tile with its cold rows arriving in the stage (started one
@@ -504,7 +512,7 @@ __device__ __forceinline__ void tile_async(const EpochArgs &p, unsigned char *sm
     const bool bad = own_next.decode(p, next_rc);
     if (__any_sync(FULL, bad) && lane == 0) atomicOr(p.err, ERRBIT_INDEX);
     if (aborted) own_next.valid = false;
-    stage_issue<N>(p, own_next, stage, 32 * q + lane, sbar);
+    stage_issue<N>(p, own_next, stage, q, lane, sbar);
   }
   if (!active) return;
   if (issuer && !aborted) {
@@ -622,7 +630,8 @@ __device__ __forceinline__ void tile_async(const EpochArgs &p, unsigned char *sm
 // number of nonzeros per CTA as k_factor.  A timed-out MMA wait latches
 // ERRBIT_TIMEOUT; the CTA stops at its next window boundary and frees TMEM.
 // ASYNC (hot-row cache on, every row full width, one step size): the rows
-// of the next tile arrive in a per-warpgroup stage by bulk copies (tile_async).
+// of the next tile arrive in a per-warpgroup stage by asynchronous copies
+// (stage_issue, tile_async).
 template <int N, bool ASYNC = false>
 __global__ void __launch_bounds__(tc::THREADS, 1) k_factor_tc(const EpochArgs p) {
   using L = tc::Smem<N>;
@@ -688,7 +697,7 @@ __global__ void __launch_bounds__(tc::THREADS, 1) k_factor_tc(const EpochArgs p)
       rc.load(p, row_of(blockIdx.x));
       const bool bad = d0.decode(p, rc);
       if (__any_sync(FULL, bad) && lane == 0) atomicOr(p.err, ERRBIT_INDEX);
-      tc::stage_issue<N>(p, d0, stage, 32 * q + lane, sbar);
+      tc::stage_issue<N>(p, d0, stage, q, lane, sbar);
     }
     if (blockIdx.x + G < nct) rc.load(p, row_of(blockIdx.x + G));
     int k = 0;
@@ -719,6 +728,7 @@ __global__ void __launch_bounds__(tc::THREADS, 1) k_factor_tc(const EpochArgs p)
     // copies started for a tile that never ran (a stop after a timeout):
     // wait for them, with a limit, before the CTA leaves
     if (pending) (void)tc::wait_parity(sbar, sphase);
+    asm volatile("cp.async.wait_all;" ::: "memory");
   } else {
   tc::RowCoord<N> cur, nxt;
   if (blockIdx.x < nct) cur.load(p, p.begin + (int64_t(blockIdx.x) * tc::WGS + wg) * tc::TM + 32 * q + lane);
