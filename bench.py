@@ -826,7 +826,8 @@ def main():
                     help="epochs of the plain FP32 run that sets the time-to-RMSE target")
     ap.add_argument("--hot-rows", type=int, default=None,
                     help="rows per mode in the shared-memory hot-row cache (-1 auto, 0 off)")
-    ap.add_argument("--hot-window", type=int, default=None, help="CTA tiles between cache write-backs")
+    ap.add_argument("--hot-window", type=int, default=None,
+                    help="cache write-back every hot_window x 128 nonzeros of a CTA")
     ap.add_argument("--engine", choices=["warp", "tcgen05"], default="warp",
                     help="factor-pass kernels: 16-nonzero warp tiles (mma.sync) or 128-nonzero "
                          "warpgroup tiles (tcgen05.mma, TMEM)")

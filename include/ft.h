@@ -99,7 +99,8 @@ typedef struct {
   /* FT_HOGWILD only: shared-memory write-back cache of the most frequent rows
    * of the tensor (ranked over all modes by their number of training
    * nonzeros).  Each CTA keeps hot_rows rows in shared memory, updates them
-   * there, and every hot_window CTA tiles (8 warps x 16 nonzeros) adds its
+   * there, and after every hot_window x 128 of its nonzeros (rounded up to
+   * whole CTA tiles: 16 nonzeros per warp, 128 per tcgen05 warpgroup) adds its
    * weighted change of every dirty row (cached row minus the copy it read at
    * the last refresh) to the row in A with float atomics and refreshes its
    * copy: no CTA overwrites another CTA's change, and a CTA sees the others'
@@ -110,10 +111,15 @@ typedef struct {
    * change it), since adding them would apply the same move once per CTA.
    * The weights come from the row counts at ft_init.  The workspace holds
    * each CTA's copy (CTAs x hot_rows x K floats).  Only rows with at least
-   * hot_min_count training nonzeros are cached.  hot_rows: -1 = as many as
-   * 96 KB hold, 0 = off. */
+   * hot_min_count training nonzeros are cached.  With the cache on, the
+   * warp-tile pass runs one 512-thread CTA per SM where its tile fits 128
+   * registers (K = 16 and N <= 3; one cache of twice the rows instead of two
+   * CTAs' copies of the same rows), else 256-thread CTAs.  hot_rows: -1 = as
+   * many as 96 KB per 256 threads of the CTA hold (3024 rows at K = 16,
+   * N <= 3; for the tcgen05 pass with full-width rows, as many of 96 KB as
+   * fit beside its 4 x N x 8 KB row stage), 0 = off. */
   int hot_rows;
-  int hot_window;      /* >= 1; default 128 */
+  int hot_window;      /* 1 .. 2^20; default 128 */
   int hot_min_count;   /* >= 1; default 2 */
   /* Kernel family of the Hogwild factor pass: FT_ENGINE_WARP (default) = one
    * warp per 16-nonzero tile with mma.sync products; FT_ENGINE_TCGEN05 = one

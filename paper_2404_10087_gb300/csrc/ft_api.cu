@@ -336,6 +336,8 @@ struct Plan {
   ft::EvalSet es;
   int grid_factor = 0, grid_core = 0, grid_eval = 0;
   int grid_factor_tc = 0;            // tcgen05 factor pass (engine FT_ENGINE_TCGEN05)
+  int factor_threads = 256;          // CTA of the Hogwild warp-tile pass
+  int grid_delta = 0;                // deterministic per-nonzero steps (256-thread CTAs)
   int64_t det_S = 0, nbatches = 0;
   int hot_cap = 0;                   // cache slots, all modes (0 = no cache)
   size_t factor_smem = 0;            // Hogwild pass, tables + cache
@@ -354,8 +356,9 @@ struct Plan {
   int core_threads = 256;
 };
 
-// Shared memory of the hot-row cache: with two 256-thread CTAs per SM (the
-// register limit of the factor pass) each CTA can hold about 100 KB.
+// Default shared memory of the hot-row cache per 256 threads of the factor
+// CTA: two 256-thread CTAs per SM hold about 100 KB each, one 512-thread CTA
+// twice that.
 constexpr size_t kHotCacheBytes = 96 * 1024;
 constexpr size_t kMaxSmem = 227 * 1024;
 
@@ -395,7 +398,7 @@ ft_status make_plan(int N, const int64_t *I, const int *J, int R, int64_t nnz, c
   if (c.scatter != FT_HOGWILD && c.scatter != FT_DETERMINISTIC) return FT_ERR_ARG;
   if (c.scatter == FT_DETERMINISTIC && c.det_batch < 1) return FT_ERR_ARG;
   if (c.blocks_per_sm < 0) return FT_ERR_ARG;
-  if (c.hot_rows < -1 || c.hot_window < 1 || c.hot_min_count < 1) return FT_ERR_ARG;
+  if (c.hot_rows < -1 || c.hot_window < 1 || c.hot_window > (1 << 20) || c.hot_min_count < 1) return FT_ERR_ARG;
   if (c.reserved[0] != 0) return FT_ERR_ARG;
   if (c.l2_persist != 0 && c.l2_persist != 1) return FT_ERR_ARG;
   if (c.core_scheme != FT_CORE_CALC && c.core_scheme != FT_CORE_STORE) return FT_ERR_ARG;
@@ -444,8 +447,10 @@ ft_status make_plan(int N, const int64_t *I, const int *J, int R, int64_t nnz, c
     const size_t per_slot = size_t(K) * sizeof(float) + 1;
     int64_t sumI = 0;
     for (int n = 0; n < N; ++n) sumI += I[n];
+    if (!tc) p->factor_threads = p->ks.factor_threads;
+    const size_t budget = tc ? kHotCacheBytes : kHotCacheBytes * size_t(p->factor_threads / 256);
     const int64_t fit = int64_t((kMaxSmem - factor_base_smem - stage_bytes - 64) / per_slot);
-    int64_t cap = c.hot_rows > 0 ? c.hot_rows : std::min<int64_t>(int64_t(kHotCacheBytes / per_slot), fit);
+    int64_t cap = c.hot_rows > 0 ? c.hot_rows : std::min<int64_t>(int64_t(budget / per_slot), fit);
     cap = std::min(cap, sumI);
     if (cap > fit) return FT_ERR_ARG;
     p->hot_cap = int(std::max<int64_t>(cap, 0));
@@ -464,8 +469,11 @@ ft_status make_plan(int N, const int64_t *I, const int *J, int R, int64_t nnz, c
     if (occ_t < 1 || occ_max * p->ks.factor_tc_tmem_cols > 512) return FT_ERR_CUDA;
     p->grid_factor_tc = p->num_sms * per_sm;
   }
-  const int occ_f = std::min(occupancy(p->ks.factor, 256, tc ? p->ks.factor_smem : p->factor_smem),
-                             occupancy(p->ks.factor_fast, 256, tc ? p->ks.factor_smem : p->factor_smem));
+  // without the cache the warp-tile pass runs 256-thread CTAs
+  if (p->hot_cap == 0) p->factor_threads = 256;
+  const int ft_threads = tc ? 256 : p->factor_threads;
+  const int occ_f = std::min(occupancy(p->ks.factor, ft_threads, tc ? p->ks.factor_smem : p->factor_smem),
+                             occupancy(p->ks.factor_fast, ft_threads, tc ? p->ks.factor_smem : p->factor_smem));
   const int occ_d = occupancy(p->ks.factor_delta, 256, p->ks.factor_smem);
   const bool store = c.core_scheme == FT_CORE_STORE;
   p->core_fn = store ? p->ks.core_store : p->ks.core;
@@ -476,7 +484,8 @@ ft_status make_plan(int N, const int64_t *I, const int *J, int R, int64_t nnz, c
   const int occ_e = occupancy(p->es.errors, 256, p->es.smem);
   if (occ_f < 1 || occ_d < 1 || occ_c < 1 || occ_p < 1 || occ_e < 1) return FT_ERR_CUDA;
   const int bps = c.blocks_per_sm;
-  p->grid_factor = p->num_sms * (bps ? bps : std::min(occ_f, occ_d));
+  p->grid_factor = p->num_sms * (bps ? bps : occ_f);
+  p->grid_delta = p->num_sms * (bps ? bps : occ_d);
   p->grid_core = p->num_sms * std::min(bps ? bps : occ_c, kMaxCoreBlocksPerSm);
   p->grid_eval = p->num_sms * std::min(occ_p, occ_e);
 
@@ -758,16 +767,17 @@ ft_status build_hot_cache(ft_ctx *c, cudaStream_t st) {
     return a.n != b.n ? a.n < b.n : a.r < b.r;
   });
   // Write-back weight of every slot.  A CTA handles n_w nonzeros between two
-  // write-backs (hot_window CTA tiles of 128 nonzeros, or its whole share of
-  // a small tensor).  A row with c of the nnz nonzeros appears x = c n_w /
+  // write-backs (hot_window x 128 nonzeros rounded up to whole CTA tiles, or
+  // its whole share of a small tensor).  A row with c of the nnz nonzeros appears x = c n_w /
   // nnz times in that share, and P = G (1 - (1 - c / nnz)^n_w) of the G CTAs
   // are expected to change it between write-backs.  x < 1: the CTAs' changes
   // are distinct steps of distinct nonzeros and add up (w = 1, Hogwild);
   // x >= 1: every CTA moves the row several steps toward the same optimum
   // and the row takes their average (w = 1 / P).
   const int G = p.cfg.engine == FT_ENGINE_TCGEN05 ? p.grid_factor_tc : p.grid_factor;
-  const double n_w = std::min<double>(double(p.cfg.hot_window) * 128.0,
-                                      std::ceil(double(p.nnz) / double(std::max(G, 1))));
+  const int64_t tile = p.cfg.engine == FT_ENGINE_TCGEN05 ? 512 : 16 * (p.factor_threads / 32);
+  const int64_t per_window = (int64_t(p.cfg.hot_window) * 128 + tile - 1) / tile * tile;
+  const double n_w = std::min<double>(double(per_window), std::ceil(double(p.nnz) / double(std::max(G, 1))));
   std::vector<float> weight(std::max<size_t>(k, 1), 1.f);
   for (size_t q = 0; q < k; ++q) {
     const double cnt = double(cand[q].count), nnz = double(std::max<int64_t>(p.nnz, 1));
@@ -931,7 +941,7 @@ ft_status ft_epoch_factors(ft_ctx *c, float lr_a, float lambda_a, const float *c
     if (p.cfg.engine == FT_ENGINE_TCGEN05)
       return launch(c, fast ? p.ks.factor_tc_async : p.ks.factor_tc, p.grid_factor_tc, p.ks.factor_tc_threads,
                     c->hot_active ? p.factor_smem : p.ks.factor_tc_smem, &a, st);
-    return launch(c, fast ? p.ks.factor_fast : p.ks.factor, p.grid_factor, 256,
+    return launch(c, fast ? p.ks.factor_fast : p.ks.factor, p.grid_factor, p.factor_threads,
                   c->hot_active ? p.factor_smem : p.ks.factor_smem, &a, st);
   }
 
@@ -955,7 +965,7 @@ ft_status ft_epoch_factors(ft_ctx *c, float lr_a, float lambda_a, const float *c
     a.begin = b * p.det_S;
     a.end = std::min(p.nnz, a.begin + p.det_S);
     const int64_t tiles = (a.end - a.begin + FT_TILE - 1) / FT_TILE;
-    const int grid = int(std::min<int64_t>(p.grid_factor, (tiles + 7) / 8));
+    const int grid = int(std::min<int64_t>(p.grid_delta, (tiles + 7) / 8));
     ft_status s = launch(c, p.ks.factor_delta, grid, 256, p.ks.factor_smem, &a, st);
     if (s != FT_OK) return s;
     ap.thread_off[0] = 0;

@@ -73,7 +73,7 @@ struct EpochArgs {
   const int32_t *hot_rows;
   int hot_base[FT_MAXN + 1];
   int hot_cap;                      // slots in shared memory (0 = no cache)
-  int hot_window;                   // CTA tiles between write-back/refresh
+  int hot_window;                   // write-back/refresh every hot_window x 128 nonzeros of a CTA
   // Per-CTA copy of the cached rows as the CTA last read them from global
   // memory ([grid][hot_cap][K] floats, workspace): the write-back adds the
   // CTA's own change (cache - copy), times the slot's weight, instead of
@@ -821,8 +821,9 @@ __device__ __forceinline__ void factor_tile_fast(const EpochArgs &p, const float
 // next reads into slow coherence misses, and the stores themselves queue on
 // the hottest lines.  So the hottest rows of every mode (chosen at ft_init
 // from the row counts) live in a per-CTA write-back cache in shared memory:
-// the CTA's warps read and update the cached copy, and every hot_window CTA
-// tiles the CTA adds its weighted change of every dirty row to global memory
+// the CTA's warps read and update the cached copy, and after every
+// hot_window x 128 of its nonzeros the CTA adds its weighted change of every
+// dirty row to global memory
 // (float atomics, so no CTA overwrites another's change; see
 // cache_write_back) and refreshes its copy.
 // Rows outside the cache are stored back with plain stores: concurrent
@@ -834,8 +835,20 @@ __device__ __forceinline__ void factor_tile_fast(const EpochArgs &p, const float
 // deterministic batch reduction; A is not modified.
 // FAST (Hogwild with the hot-row cache, every mode full width, one step size
 // for every row): the tiles run factor_tile_fast.
+//
+// CTA shape: where the tile fits in 128 registers (K = 16, N <= 3) the
+// cached Hogwild pass runs one 512-thread CTA per SM, so the SM's shared
+// memory holds one cache of twice the rows instead of two CTAs' copies of
+// the same rows; elsewhere two (or one) 256-thread CTAs per SM.  The window
+// is counted in the CTA's nonzeros: a write-back every hot_window x 128 of
+// them, rounded up to whole CTA tiles.
+template <int N, int K, int MATH>
+struct FactorLaunch {
+  static constexpr int THREADS = (K == 16 && N <= 3) ? 512 : 256;
+};
+
 template <int N, int K, int MATH, bool DELTA, bool FAST = false>
-__global__ void __launch_bounds__(256) k_factor(const EpochArgs p) {
+__global__ void __launch_bounds__(FactorLaunch<N, K, MATH>::THREADS) k_factor(const EpochArgs p) {
   extern __shared__ __align__(16) float smem[];
   using L = FactorSmem<N, K, MATH>;
   fill_tables<N, K, MATH>(smem, p, true);
@@ -869,7 +882,7 @@ __global__ void __launch_bounds__(256) k_factor(const EpochArgs p) {
   // CTA tile c = warp tiles [c * wpc, c * wpc + wpc); CTA b takes c = b, b + G, ...
   const int64_t nct = (ntiles + wpc - 1) / wpc;
   const int64_t G = gridDim.x;
-  const int W = p.hot_window > 0 ? p.hot_window : 1;
+  const int W = p.hot_window > 0 ? (p.hot_window * 128 + wpc * FT_TILE - 1) / (wpc * FT_TILE) : 1;
   const int wid = threadIdx.x >> 5;
   TileCoords<N> cur, nxt;
   if (blockIdx.x < nct) cur.load(p, p.begin + (int64_t(blockIdx.x) * wpc + wid) * FT_TILE, lane, true);

@@ -39,6 +39,7 @@ ft::KernelSet make_set() {
   s.factor_delta = reinterpret_cast<const void *>(&ft::k_factor<N, FT_K, FT_MATH, true>);
   s.core = reinterpret_cast<const void *>(&ft::k_core<N, FT_K, FT_KMATH>);
   s.factor_smem = ft::FactorSmem<N, FT_K, FT_MATH>::tables();
+  s.factor_threads = ft::FactorLaunch<N, FT_K, FT_MATH>::THREADS;
   s.core_smem = ft::CoreSmem<N, FT_K, FT_KMATH>::bytes();
   s.core_threads = 32 * ft::CoreSmem<N, FT_K, FT_KMATH>::WARPS;
   s.batch_factor = reinterpret_cast<const void *>(&ft::k_batch_factor<N, FT_K, FT_MATH>);

@@ -18,6 +18,7 @@ struct KernelSet {
   // float32 rows; equal results); `core` itself at FP32 and TF32
   const void *core_f32rows = nullptr;
   size_t factor_smem = 0;              // tables only; the hot-row cache adds to it
+  int factor_threads = 256;            // CTA of the cached Hogwild pass (FactorLaunch)
   size_t core_smem = 0;
   int core_threads = 256;
   // core-gradient pass of the storage scheme (rows of C = A B precomputed)
