@@ -379,9 +379,11 @@ ft_status ft_rmse(ft_ctx *ctx, int64_t n, const int32_t *const *idx, const float
  *   rows, in/out; NULL = no history, ema = |g| / count);
  *   labels[r] (NULL = not computed): the exact line-search step along -g of
  *   the row's subproblem sum_m [1/2 (x_m - a.p_m)^2 + 1/2 lambda_a |a|^2],
- *   |g|^2 / (sum_m (p_m.g)^2 + lambda_a count |g|^2), divided by lr_a,
- *   clipped to [1/16, 16], as its natural log (the regression target of the
- *   step-size network; 0 for rows without nonzeros).
+ *   t* = |g|^2 / (sum_m (p_m.g)^2 + lambda_a count |g|^2), shared among the N
+ *   rows that every nonzero moves at once (t* / N: each row's exact step alone
+ *   would remove the residual, N of them together N times over), divided by
+ *   lr_a, clipped to [1/16, 16], as its natural log (the regression target of
+ *   the step-size network; 0 for rows without nonzeros).
  * FP32 with atomic accumulation (the summation order varies between runs). */
 ft_status ft_row_stats(ft_ctx *ctx, float lambda_a, float lr_a, float ema_beta, float *ema,
                        float *features, float *labels, void *stream);

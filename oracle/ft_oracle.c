@@ -475,10 +475,12 @@ int orc_objective(int N, const int64_t *I, const int *J, int R, double *const *A
  * Features: f0 = log(1 + count_r), f1 = log(1 + ema_r), f2 = ebar_r.
  * Label: the exact line-search step of the row's convex subproblem
  *   F_r(a) = sum_m [1/2 (x_m - a.p_m)^2 + 1/2 lambda |a|^2]
- * along -g_r:  t* = |g|^2 / (sum_m (p_m.g)^2 + lambda count |g|^2), expressed
- * as a multiplier of the epoch's SGD step gamma * g:  s* = t* / gamma, clipped
- * to [1/16, 16]; the label is log s* (rows without nonzeros, or with g = 0,
- * get log 1 = 0).
+ * along -g_r:  t* = |g|^2 / (sum_m (p_m.g)^2 + lambda count |g|^2).  Every
+ * nonzero moves its N rows at once, and each row's exact step alone would
+ * remove the nonzero's residual, so together they would remove it N times
+ * over; the row's share is t* / N.  Expressed as a multiplier of the epoch's
+ * SGD step gamma * g:  s* = t* / (N gamma), clipped to [1/16, 16]; the label
+ * is log s* (rows without nonzeros, or with g = 0, get log 1 = 0).
  * Rows of all modes are concatenated (mode 0 first).
  * ====================================================================== */
 #define ORC_SMIN (1.0 / 16.0)
@@ -559,7 +561,7 @@ int orc_row_stats(int N, const int64_t *I, const int *J, int R, double *const *A
         double s = 1.0;
         double den = hsum[q] + lambda * k * gg;
         if (k > 0.0 && gg > 0.0 && den > 0.0) {
-          s = gg / den / gamma;
+          s = gg / den / ((double)N * gamma);
           if (s < ORC_SMIN) s = ORC_SMIN;
           if (s > ORC_SMAX) s = ORC_SMAX;
         }

@@ -296,9 +296,9 @@ struct RowFinishArgs {
 
 // Features and labels of every row from the accumulated statistics:
 // f0 = log(1 + count), f1 = log(1 + ema of |g| / count), f2 = mean residual;
-// label = log of the exact line-search step along -g of the row's subproblem
-// divided by the step size, clipped to [1/16, 16] (0 for rows without
-// nonzeros).
+// label = log of the exact line-search step along -g of the row's subproblem,
+// shared among the N rows that every nonzero moves at once (divided by N),
+// over the step size, clipped to [1/16, 16] (0 for rows without nonzeros).
 __global__ void k_row_finish(const RowFinishArgs a) {
   const int64_t q = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (q >= a.roff[a.N]) return;
@@ -318,7 +318,7 @@ __global__ void k_row_finish(const RowFinishArgs a) {
   if (a.label) {
     float sc = 1.f;
     const float den = a.hsum[q] + a.lambda * k * gg;
-    if (k > 0.f && gg > 0.f && den > 0.f) sc = fminf(fmaxf(gg / den / a.gamma, 1.f / 16.f), 16.f);
+    if (k > 0.f && gg > 0.f && den > 0.f) sc = fminf(fmaxf(gg / den / (float(a.N) * a.gamma), 1.f / 16.f), 16.f);
     a.label[q] = logf(sc);
   }
 }

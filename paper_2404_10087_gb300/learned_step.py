@@ -6,8 +6,9 @@ network (3 -> 64 -> 64 -> 1, BF16 weights, FP32 accumulation) that maps row
 statistics - nonzeros in the row, a running average of the row-gradient
 norm, the mean residual - to a multiplier in [1/16, 16] (it predicts the
 log-multiplier).  The network is trained on traces of plain runs, with the
-log of the exact line-search step of every row's subproblem, relative to the
-step size, as the label (see ft_row_stats in include/ft.h).
+log of the exact line-search step of every row's subproblem, shared among
+the N rows that each nonzero moves at once and relative to the step size, as
+the label (see ft_row_stats in include/ft.h).
 
 Every step runs in the CUDA library (ft_row_stats, ft_stepnet_*,
 ft_epoch_factors with row_step_scale); this module only sequences calls.
@@ -69,7 +70,7 @@ class LearnedStep:
     """Per-row multipliers for one model, refreshed from its statistics."""
 
     def __init__(self, model: ft.FastTuckerPlus, net: torch.Tensor, lr_a: float, lam_a: float,
-                 beta: float = 0.9):
+                 beta: float = 0.9, record: bool = False):
         dev = model.vals.device
         self.model, self.net = model, net
         self.lr_a, self.lam_a, self.beta = lr_a, lam_a, beta
@@ -78,10 +79,13 @@ class LearnedStep:
         self.feat = torch.empty(rows, 3, dtype=torch.float32, device=dev)
         self.scale = torch.ones(rows, dtype=torch.float32, device=dev)
         self.per_mode = split_rows(model, self.scale)
+        self.used = [] if record else None   # the multipliers of every epoch, when recorded
 
     def refresh(self):
         ft.ft_row_stats(self.model.ctx, self.lam_a, self.lr_a, self.beta, self.ema, self.feat, None)
         ft.ft_stepnet_forward(self.net, self.feat, self.scale)
+        if self.used is not None:
+            self.used.append(self.scale.clone())
 
     def epoch(self, lr_b: float, lam_b: float):
         """Refresh the multipliers, then one factor epoch with them and one core epoch."""
@@ -139,28 +143,33 @@ def ab_study(make_model, tei, xte, lrs, lam, lr_b, lam_b, epochs=20, trace_epoch
       * learned: eta* times the per-row multipliers (refreshed every epoch;
         the statistics and network passes are timed with it);
       * constant: plain SGD at eta* times the learned run's mean multiplier
-        (the same global scale without the per-row part).
+        over its rows and epochs (the same global scale without the per-row
+        part).
     Reported with the plain sweep's own time to the target at every step
-    size (the best fixed step is the fastest of them), the label
-    distribution (share at the clip), the spread of the multipliers over the
-    rows, and the trained network's loss against the best constant
-    predictor's (the labels' variance)."""
+    size (the best fixed step is the fastest of the runs that did not
+    diverge), the label distribution (share at the clip), the spread of the
+    multipliers the learned run used (all its rows and epochs), and the
+    trained network's loss against the best constant predictor's (the
+    labels' variance)."""
     sweep = {}
     for lr in lrs:
         m = make_model(1)
         ep, t, r, curve = _timed_run(lambda: (m.epoch_factors(lr, lam), m.epoch_core(lr_b, lam_b)), m, tei, xte,
                                      epochs)
-        sweep[lr] = {"final_test_rmse": r, "seconds": t, "curve": curve}
+        sweep[lr] = {"final_test_rmse": r, "seconds": t, "epochs_run": ep, "curve": curve}
         m.close()
     finite = {lr: v for lr, v in sweep.items() if v["final_test_rmse"] < float("inf")}
     eta = min(finite, key=lambda lr: finite[lr]["final_test_rmse"])
     target = sweep[eta]["final_test_rmse"]
     for lr, v in sweep.items():
         k = _epochs_to(v["curve"], target)
-        v["seconds_to_target"] = (v["seconds"] * k / epochs) if k is not None else None
+        # seconds cover the epochs the run made (a diverged run stops early)
+        v["seconds_to_target"] = (v["seconds"] * k / max(v["epochs_run"], 1)) if k is not None else None
         v["curve"] = [round(c, 5) if c < float("inf") else "diverged" for c in v["curve"]]
-    reaching = [v["seconds_to_target"] for v in sweep.values() if v["seconds_to_target"] is not None]
-    best_fixed = min(reaching)
+    # the best fixed step: the fastest to the target among the steps whose
+    # run did not diverge
+    best_fixed = min(v["seconds_to_target"] for lr, v in sweep.items()
+                     if lr in finite and v["seconds_to_target"] is not None)
     # the trace run from another start; at a step on the edge of stability it
     # may diverge from there, and then the next smaller step of the grid
     # gives the traces (the labels stay relative to eta*, the learned run's
@@ -182,9 +191,11 @@ def ab_study(make_model, tei, xte, lrs, lam, lr_b, lam_b, epochs=20, trace_epoch
     net = ft.new_stepnet(feats.device, seed=seed)
     loss_curve = train(net, feats, labels, steps=train_steps)
     model = make_model(1)
-    learned = LearnedStep(model, net, eta, lam)
+    learned = LearnedStep(model, net, eta, lam, record=True)
     ep_l, t_l, r_l, curve_l = _timed_run(lambda: learned.epoch(lr_b, lam_b), model, tei, xte, epochs, target)
-    logs = learned.scale.double().log()
+    # the multipliers the run used, over all its epochs and rows
+    logs = torch.cat(learned.used).double().log()
+    logs = logs[torch.isfinite(logs)]
     model.close()
     mean_mult = float(logs.exp().mean())
     cm = make_model(1)

@@ -4,7 +4,10 @@ labels, step-size network) against independent computations:
 * counts by np.bincount, residuals and row gradients by central finite
   differences of the row's subproblem loss through the dense Tucker model;
 * the label is the log of the exact minimiser along -g of that (quadratic)
-  subproblem, recovered from three loss evaluations, over the step size;
+  subproblem, recovered from three loss evaluations, over N times the step
+  size; and on a tensor whose rows each hold one nonzero, the N rows of a
+  nonzero stepping together by their labels remove its residual to first
+  order (without the 1/N they would flip its sign: e -> (1 - N) e);
 * the network's forward pass equals the textbook MLP written with numpy
   matrix products (linear output u, multiplier exp(clamp(u))), and its
   gradient equals central finite differences of mean 1/2 (u - y)^2 computed
@@ -68,9 +71,59 @@ def test_row_stats_against_definitions():
             fp = row_loss(A, B, idx, x, lam, n, r, A[n][r] - dlt * g)
             fm = row_loss(A, B, idx, x, lam, n, r, A[n][r] + dlt * g)
             t_star = dlt * (fm - fp) / (2 * (fp - 2 * f0 + fm))
-            want = float(np.log(np.clip(t_star / gamma, 1 / 16, 16)))
+            want = float(np.log(np.clip(t_star / (N * gamma), 1 / 16, 16)))
             assert np.isclose(lab[q], want, rtol=1e-5, atol=1e-6), (n, r, lab[q], want)
         off += I[n]
+
+
+def test_labels_share_the_step_among_the_modes():
+    """Every row holds one nonzero and lambda = 0, so each row's exact step
+    alone would remove its nonzero's residual.  The N rows of a nonzero
+    stepping together by gamma exp(label) g (g by central differences of the
+    dense model) leave a residual of second order in e; the same steps
+    without the 1/N leave (1 - N) e."""
+    rng = np.random.default_rng(11)
+    for N, J, R in [(3, (2, 3, 2), 3), (4, (2, 2, 3, 2), 2)]:
+        M = 12
+        I = [M] * N
+        A = [rng.normal(0, 0.8, (M, J[n])) for n in range(N)]
+        B = [rng.normal(0, 0.8, (J[n], R)) for n in range(N)]
+        idx = np.stack([rng.permutation(M) for _ in range(N)]).astype(np.int32)
+        xhat = np.array([dense_predict(A, B, idx[:, m]) for m in range(M)])
+        e = 1e-3 * rng.choice([-1.0, 1.0], M) * (1 + rng.uniform(0, 1, M))
+        x = xhat + e
+        gamma = 1.0
+        _, lab = oracle.row_stats(A, B, idx, x, 0.0, gamma, 0.0, None)
+        lo, hi = np.log(1 / 16), np.log(16)
+        checked = 0
+        h = 1e-6
+        for m in range(M):
+            q = [n * M + idx[n, m] for n in range(N)]
+            if not all(lo + 1e-9 < lab[v] < hi - 1e-9 for v in q):
+                continue
+            steps = []
+            for n in range(N):
+                r = idx[n, m]
+                dx = np.zeros(J[n])
+                for j in range(J[n]):
+                    Ap = [a.copy() for a in A]
+                    Am = [a.copy() for a in A]
+                    Ap[n][r, j] += h
+                    Am[n][r, j] -= h
+                    dx[j] = (dense_predict(Ap, B, idx[:, m]) - dense_predict(Am, B, idx[:, m])) / (2 * h)
+                g = -e[m] * dx
+                steps.append(gamma * np.exp(lab[q[n]]) * g)
+            # second-order terms grow with the step: 2% of e for the shared
+            # steps, 10% for the N times larger ones (both far from the
+            # other case's value, |(1 - N) e| >= 2 |e|)
+            for mult, want, tol in ((1.0, 0.0, 2e-2), (float(N), (1 - N) * e[m], 1e-1)):
+                A2 = [a.copy() for a in A]
+                for n in range(N):
+                    A2[n][idx[n, m]] -= mult * steps[n]
+                e2 = x[m] - dense_predict(A2, B, idx[:, m])
+                assert abs(e2 - want) <= tol * abs(e[m]), (N, m, mult, e2, want, e[m])
+            checked += 1
+        assert checked >= M // 2, checked
 
 
 def mlp_numpy_raw(P, X):
@@ -122,7 +175,8 @@ def test_mlp_gradient_by_central_differences():
 
 
 STEPNET_PINS = [test_row_stats_against_definitions, test_mlp_forward_is_the_textbook_network,
-                test_mlp_gradient_by_central_differences]
+                test_mlp_gradient_by_central_differences,
+                test_labels_share_the_step_among_the_modes]
 STEPNET_MUTANTS = [
     ("label_without_regulariser_curvature", "double den = hsum[q] + lambda * k * gg;", "double den = hsum[q];"),
     ("relu_derivative_dropped", "double dh2 = h2[i] > 0.0 ? dz * w3[i] : 0.0;", "double dh2 = dz * w3[i];"),
@@ -131,6 +185,7 @@ STEPNET_MUTANTS = [
     ("row_gradient_sign", "g[goff[n] + row * J[n] + j] += -e * pj + lambda * a[j];",
      "g[goff[n] + row * J[n] + j] += e * pj + lambda * a[j];"),
     ("mean_residual_not_divided", "feat[3 * q + 2] = k > 0.0 ? esum[q] / k : 0.0;", "feat[3 * q + 2] = esum[q];"),
+    ("label_step_not_shared", "s = gg / den / ((double)N * gamma);", "s = gg / den / gamma;"),
 ]
 
 
