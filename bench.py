@@ -45,6 +45,7 @@ WORKLOAD = "netflix_shaped_zipf_1e8"
 # Algorithm 5 divides the summed gradient by |Omega|.
 LR = 0.04          # factor step gamma_A
 LR_B = 0.3         # core step gamma_B
+LR_ORDERS = 0.01   # factor step of the synthetic order sweep
 LAM = 0.01
 FALLBACK_HBM_GBS = 6800.0
 
@@ -488,18 +489,18 @@ def run_ours(args, rank, world, local_rank):
     return out
 
 
-def time_phases(m, steps, warmup, stream):
+def time_phases(m, steps, warmup, stream, lr=LR):
     """Median factor-pass and core-pass times (CUDA events) over `steps`
     factor + core epochs after `warmup` untimed ones."""
     for _ in range(warmup):
-        m.epoch_factors(LR, LAM)
+        m.epoch_factors(lr, LAM)
         m.epoch_core(LR_B, LAM)
     torch.cuda.synchronize()
     rec = []
     for _ in range(steps):
         e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
         e[0].record(stream)
-        m.epoch_factors(LR, LAM)
+        m.epoch_factors(lr, LAM)
         e[1].record(stream)
         m.epoch_core(LR_B, LAM)
         e[2].record(stream)
@@ -533,17 +534,24 @@ def run_sweep(args, local_rank):
     peak, peak_kind = peak_hbm()
     rows = []
     if args.sweep in ("orders", "all"):
+        # the synthetic orders share one factor step, small enough that no
+        # order diverges (the Netflix-shaped step 0.04 diverged at high order:
+        # every row there meets 1e4 nonzeros per epoch)
         for N in range(3, 11):
             w = synth.synthetic_order(N, nnz=args.nnz or 100_000_000)
             w_, tri, trx, tei, tex, A, B = make_workload(dev, None, w)
             eng = engine_for(args, N, 16, 16)
             m = ft.FastTuckerPlus(tri, trx, A, B, precision=args.precision, hot_rows=args.hot_rows,
                                   hot_window=args.hot_window, engine=eng)
-            f, c = time_phases(m, args.steps, args.warmup, stream)
+            f, c = time_phases(m, args.steps, args.warmup, stream, lr=LR_ORDERS)
             nnz = int(trx.numel())
-            rmse = m.rmse(tei, tex)[0]
+            try:
+                rmse = m.rmse(tei, tex)[0]
+            except ft.FtError:
+                rmse = "diverged"
             per = algorithmic_bytes_factor(N, w.J)
             rows.append({"study": "order", "N": N, "I": w.I[0], "J": 16, "R": 16, "engine": eng, "nnz_train": nnz,
+                         "lr_a": LR_ORDERS,
                          "factor_ms": f, "core_ms": c, "value": nnz / ((f + c) / 1e3),
                          "factor_frac_hbm": per * nnz / (f / 1e3) / 1e9 / peak, "test_rmse": rmse})
             m.close()

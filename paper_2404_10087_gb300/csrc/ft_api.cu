@@ -542,6 +542,7 @@ struct ft_ctx {
   float *B[FT_MAXN] = {nullptr};
   char *ws = nullptr;
   unsigned vecmask = 0;
+  unsigned vec4mask = 0;
   std::vector<int64_t> seg_lo[FT_MAXN];  // per mode: first segment of each batch (+ end)
   int hot_base[FT_MAXN + 1] = {0};       // cache slots of mode n: [base[n], base[n+1])
   bool hot_active = false;
@@ -633,6 +634,7 @@ ft::EpochArgs base_args(ft_ctx *c) {
   a.R = c->p.R;
   a.sumJ = c->p.sumJ;
   a.vecmask = c->vecmask;
+  a.vec4mask = c->vec4mask;
   a.vals = c->vals;
   a.begin = 0;
   a.end = c->p.nnz;
@@ -868,8 +870,10 @@ ft_status ft_init(ft_ctx **out, int N, const int64_t *I, const int *J, int R, in
     c->idx[n] = idx[n];
     c->A[n] = A[n];
     c->B[n] = B[n];
-    // full 16-byte row chunks: rows exactly K wide and a 16-byte aligned base
+    // full 16-byte row chunks: rows exactly K wide and a 16-byte aligned base;
+    // 16-byte groups of narrower rows: J_n a multiple of 4 and that base
     if (J[n] == c->p.K && (reinterpret_cast<uintptr_t>(A[n]) % 16) == 0) c->vecmask |= 1u << n;
+    if (J[n] % 4 == 0 && (reinterpret_cast<uintptr_t>(A[n]) % 16) == 0) c->vec4mask |= 1u << n;
   }
   c->vals = vals;
   c->ws = static_cast<char *>(workspace);
@@ -1273,6 +1277,7 @@ ft_status ft_core_grad_noalloc(int N, const int64_t *I, const int *J, int R, int
     a.J[n] = J[n];
     a.offJ[n] = p.offJ[n];
     if (J[n] == p.K && (reinterpret_cast<uintptr_t>(A[n]) % 16) == 0) a.vecmask |= 1u << n;
+    if (J[n] % 4 == 0 && (reinterpret_cast<uintptr_t>(A[n]) % 16) == 0) a.vec4mask |= 1u << n;
   }
   a.R = R;
   a.sumJ = p.sumJ;

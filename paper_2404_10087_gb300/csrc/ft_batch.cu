@@ -482,6 +482,7 @@ ft_status ft_batch_init(ft_batch **out, int ntensors, const ft_tensor_desc *tens
       a.offJ[n] = offJ;
       offJ += ti.J[n];
       if (ti.J[n] == ti.K && (reinterpret_cast<uintptr_t>(ti.A[n]) % 16) == 0) a.vecmask |= 1u << n;
+      if (ti.J[n] % 4 == 0 && (reinterpret_cast<uintptr_t>(ti.A[n]) % 16) == 0) a.vec4mask |= 1u << n;
     }
     a.sumJ = offJ;
     a.R = ti.R;
@@ -585,6 +586,7 @@ ft_status ft_batch_rmse(ft_batch *b, int tensor, int64_t n, const int32_t *const
     a.I[k] = ti.I[k];
     a.J[k] = ti.J[k];
     if (ti.J[k] == ti.K && (reinterpret_cast<uintptr_t>(ti.A[k]) % 16) == 0) a.vecmask |= 1u << k;
+    if (ti.J[k] % 4 == 0 && (reinterpret_cast<uintptr_t>(ti.A[k]) % 16) == 0) a.vec4mask |= 1u << k;
   }
   a.R = ti.R;
   a.vals = vals;

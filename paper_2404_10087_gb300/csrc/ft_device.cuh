@@ -59,6 +59,8 @@ struct EpochArgs {
   int R;
   int sumJ;
   unsigned vecmask;                 // bit n: rows of mode n can be read as full 16-byte chunks
+  unsigned vec4mask;                // bit n: J_n % 4 == 0 and a 16-byte aligned base, so every
+                                    // 4-column group of a row is one 16-byte access
   const float *vals;                // values
   int64_t begin, end;               // processed nonzero range [begin, end)
   float lr, lam;
@@ -252,6 +254,36 @@ struct Prod<K, MATH_TF32X3> {
   }
   __device__ static void run(const float (&x)[2][CPL], const float *tabf, float (&y)[2][CPL], int lane) {
     const uint4 *tab = reinterpret_cast<const uint4 *>(tabf);
+    if constexpr (K == 32) {
+      // k-steps outside, n-tiles inside: only one k-step's split operands
+      // are live (8 registers instead of 4 K), for the register-bound K = 32
+      // tiles; per n-tile the three products of a k-step are added tail
+      // terms first
+      float acc[NT][4];
+#pragma unroll
+      for (int u = 0; u < NT; ++u) acc[u][0] = acc[u][1] = acc[u][2] = acc[u][3] = 0.f;
+#pragma unroll
+      for (int s = 0; s < KS; ++s) {
+        uint32_t h[4], l[4];
+        split(x[0][2 * s], h[0], l[0]);
+        split(x[1][2 * s], h[1], l[1]);
+        split(x[0][2 * s + 1], h[2], l[2]);
+        split(x[1][2 * s + 1], h[3], l[3]);
+#pragma unroll
+        for (int u = 0; u < NT; ++u) {
+          const uint4 b = tab[(u * KS + s) * 32 + lane];
+          mma_tf32(acc[u], l[0], l[1], l[2], l[3], b.x, b.y);
+          mma_tf32(acc[u], h[0], h[1], h[2], h[3], b.z, b.w);
+          mma_tf32(acc[u], h[0], h[1], h[2], h[3], b.x, b.y);
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < NT; ++u) {
+        y[0][2 * u] = acc[u][0]; y[0][2 * u + 1] = acc[u][1];
+        y[1][2 * u] = acc[u][2]; y[1][2 * u + 1] = acc[u][3];
+      }
+      return;
+    }
     uint32_t xh[2][CPL], xl[2][CPL];
 #pragma unroll
     for (int q = 0; q < CPL; ++q) {
@@ -332,7 +364,7 @@ struct Prod<K, MATH_BF16> {
 // write them during the pass; the core phase may use the read-only path.
 template <int K, bool READ_ONLY>
 __device__ __forceinline__ void load_chunk(const float *__restrict__ An, int64_t row, int J, int t,
-                                           bool valid, bool vec, float (&v)[K / 4]) {
+                                           bool valid, bool vec, bool vec4, float (&v)[K / 4]) {
   constexpr int CPL = K / 4;
   if (!valid) {
 #pragma unroll
@@ -349,6 +381,19 @@ __device__ __forceinline__ void load_chunk(const float *__restrict__ An, int64_t
       else f = __ldcg(reinterpret_cast<const float4 *>(p + w));
       v[w] = f.x; v[w + 1] = f.y; v[w + 2] = f.z; v[w + 3] = f.w;
     }
+  } else if (vec4) {
+    // rows narrower than K: the 4-column groups inside the row, one 16-byte
+    // load each (J_n is a multiple of 4, so a group is wholly in or out)
+#pragma unroll
+    for (int w = 0; w < CPL; w += 4) {
+      float4 f = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (CPL * t + w < J) {
+        if constexpr (READ_ONLY || FT_FACTOR_LOAD == 2) f = __ldg(reinterpret_cast<const float4 *>(p + w));
+        else if constexpr (FT_FACTOR_LOAD == 1) f = __ldca(reinterpret_cast<const float4 *>(p + w));
+        else f = __ldcg(reinterpret_cast<const float4 *>(p + w));
+      }
+      v[w] = f.x; v[w + 1] = f.y; v[w + 2] = f.z; v[w + 3] = f.w;
+    }
   } else {
 #pragma unroll
     for (int q = 0; q < CPL; ++q) {
@@ -362,12 +407,16 @@ __device__ __forceinline__ void load_chunk(const float *__restrict__ An, int64_t
 
 template <int K>
 __device__ __forceinline__ void store_chunk(float *__restrict__ An, int64_t row, int J, int t, bool vec,
-                                            const float (&v)[K / 4]) {
+                                            bool vec4, const float (&v)[K / 4]) {
   constexpr int CPL = K / 4;
   float *p = An + row * J + CPL * t;
   if (vec) {
 #pragma unroll
     for (int w = 0; w < CPL; w += 4) __stcg(reinterpret_cast<float4 *>(p + w), make_float4(v[w], v[w + 1], v[w + 2], v[w + 3]));
+  } else if (vec4) {
+#pragma unroll
+    for (int w = 0; w < CPL; w += 4)
+      if (CPL * t + w < J) __stcg(reinterpret_cast<float4 *>(p + w), make_float4(v[w], v[w + 1], v[w + 2], v[w + 3]));
   } else {
 #pragma unroll
     for (int q = 0; q < CPL; ++q)
@@ -508,7 +557,8 @@ struct Front {
             a[n][h][w] = f4.x; a[n][h][w + 1] = f4.y; a[n][h][w + 2] = f4.z; a[n][h][w + 3] = f4.w;
           }
         } else {
-          load_chunk<K, READ_ONLY>(p.A[n], row[n][h], p.J[n], t, valid[h], (p.vecmask >> n) & 1, a[n][h]);
+          load_chunk<K, READ_ONLY>(p.A[n], row[n][h], p.J[n], t, valid[h], (p.vecmask >> n) & 1,
+                                   (p.vec4mask >> n) & 1, a[n][h]);
         }
       }
   }
@@ -621,7 +671,7 @@ __device__ void cache_refresh(const EpochArgs &p, float *rep) {
     float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
     if (slot < p.hot_base[N] && j0 < p.J[n]) {
       const float *src = p.A[n] + int64_t(__ldg(p.hot_rows + slot)) * p.J[n] + j0;
-      if (((p.vecmask >> n) & 1) != 0) {
+      if (((p.vec4mask >> n) & 1) != 0) {
         v = __ldcg(reinterpret_cast<const float4 *>(src));
       } else {
         v.x = __ldcg(src);
@@ -647,7 +697,7 @@ __device__ void cache_write_back(const EpochArgs &p, const float *rep, unsigned 
     const float w = __ldg(p.hot_weight + slot);
     const float4 d = make_float4(w * (v.x - s.x), w * (v.y - s.y), w * (v.z - s.z), w * (v.w - s.w));
     float *dst = p.A[n] + int64_t(__ldg(p.hot_rows + slot)) * p.J[n] + j0;
-    if (((p.vecmask >> n) & 1) != 0) {
+    if (((p.vec4mask >> n) & 1) != 0) {
       atomicAdd(reinterpret_cast<float4 *>(dst), d);
     } else {
       atomicAdd(dst, d.x);
@@ -720,7 +770,7 @@ __device__ __forceinline__ void factor_tile(const EpochArgs &p, const float *tab
             *reinterpret_cast<float4 *>(dst + w) = make_float4(out[w], out[w + 1], out[w + 2], out[w + 3]);
           if (t == 0) dirty[f.row[n][h]] = 1;
         } else {
-          store_chunk<K>(p.A[n], f.row[n][h], p.J[n], t, (p.vecmask >> n) & 1, out);
+          store_chunk<K>(p.A[n], f.row[n][h], p.J[n], t, (p.vecmask >> n) & 1, (p.vec4mask >> n) & 1, out);
         }
       }
     }

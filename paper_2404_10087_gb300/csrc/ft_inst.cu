@@ -22,27 +22,37 @@
 #define FT_CAT(a, b, c, d) FT_CAT_(a, b, c, d)
 
 // Arithmetic of the core-gradient kernels for the precision of this unit:
-// FT_FP32 runs them on FP32-accurate three-pass TF32 tensor-core products
-// (its factor pass stays on the CUDA cores, which measured faster there).
+// FT_FP32 runs them on FP32-accurate three-pass TF32 tensor-core products.
 #if FT_MATH == 0
 #define FT_KMATH ft::MATH_TF32X3
 #else
 #define FT_KMATH FT_MATH
 #endif
 
+// Arithmetic of the factor kernels: FT_FP32 forms a.B and d.B^T on the CUDA
+// cores at K = 16 (measured faster there than three-pass TF32) and on
+// FP32-accurate three-pass TF32 tensor-core products at K = 32, where the
+// CUDA-core form costs K^2 FMAs, K shuffles and K/2 shared loads per row and
+// product.
+#if FT_MATH == 0 && FT_K == 32
+#define FT_FMATH ft::MATH_TF32X3
+#else
+#define FT_FMATH FT_MATH
+#endif
+
 namespace {
 template <int N>
 ft::KernelSet make_set() {
   ft::KernelSet s;
-  s.factor = reinterpret_cast<const void *>(&ft::k_factor<N, FT_K, FT_MATH, false>);
-  s.factor_fast = reinterpret_cast<const void *>(&ft::k_factor<N, FT_K, FT_MATH, false, true>);
-  s.factor_delta = reinterpret_cast<const void *>(&ft::k_factor<N, FT_K, FT_MATH, true>);
+  s.factor = reinterpret_cast<const void *>(&ft::k_factor<N, FT_K, FT_FMATH, false>);
+  s.factor_fast = reinterpret_cast<const void *>(&ft::k_factor<N, FT_K, FT_FMATH, false, true>);
+  s.factor_delta = reinterpret_cast<const void *>(&ft::k_factor<N, FT_K, FT_FMATH, true>);
   s.core = reinterpret_cast<const void *>(&ft::k_core<N, FT_K, FT_KMATH>);
-  s.factor_smem = ft::FactorSmem<N, FT_K, FT_MATH>::tables();
-  s.factor_threads = ft::FactorLaunch<N, FT_K, FT_MATH>::THREADS;
+  s.factor_smem = ft::FactorSmem<N, FT_K, FT_FMATH>::tables();
+  s.factor_threads = ft::FactorLaunch<N, FT_K, FT_FMATH>::THREADS;
   s.core_smem = ft::CoreSmem<N, FT_K, FT_KMATH>::bytes();
   s.core_threads = 32 * ft::CoreSmem<N, FT_K, FT_KMATH>::WARPS;
-  s.batch_factor = reinterpret_cast<const void *>(&ft::k_batch_factor<N, FT_K, FT_MATH>);
+  s.batch_factor = reinterpret_cast<const void *>(&ft::k_batch_factor<N, FT_K, FT_FMATH>);
   s.batch_core = reinterpret_cast<const void *>(&ft::k_batch_core<N, FT_K, FT_KMATH>);
   s.batch_core_smem = ft::CoreSmem<N, FT_K, FT_KMATH>::bytes();
   s.batch_core_threads = 32 * ft::CoreSmem<N, FT_K, FT_KMATH>::WARPS;

@@ -292,6 +292,25 @@ def test_row_step_scale_deterministic():
     assert errmodel.step_errors_floor(A0, f64(gA), ref, touches, 1.0) <= 1e-4
 
 
+@pytest.mark.parametrize("cache", [dict(hot_rows=0), dict(hot_min_count=1)], ids=["no_cache", "all_rows_cacheable"])
+@pytest.mark.parametrize("precision", ["fp32", "bf16"])
+@pytest.mark.parametrize("shape", SHAPES, ids=SHAPE_IDS)
+def test_hogwild_without_collisions_every_shape(shape, precision, cache):
+    """The Hogwild pass on every parity shape - rows narrower than the padded
+    rank K among them (read and written as 16-byte groups where J_n is a
+    multiple of 4, element by element elsewhere), K = 32 with FP32-accurate
+    three-pass TF32 products - equals the sequential epoch when no two
+    nonzeros share a row, with the hot-row cache off and with every row
+    cacheable."""
+    idx, x, A, B = collision_free(shape, 31)
+    gidx, gx, gA, gB = to_dev(idx, x, A, B)
+    nnz = shape[3]
+    m = ft.FastTuckerPlus(gidx, gx, gA, gB, precision=precision, **cache)
+    m.epoch_factors(0.03, 0.02)
+    m.check()
+    check_factor_step(f64(A), f64(B), idx.numpy(), x.double().numpy(), nnz, 0.03, 0.02, f64(gA), precision)
+
+
 @pytest.mark.parametrize("cache", [dict(hot_rows=0), dict(hot_min_count=1), dict(hot_min_count=1, hot_window=1)],
                          ids=["no_cache", "all_rows_cacheable", "window_1"])
 @pytest.mark.parametrize("precision", ["fp32", "tf32", "bf16"])
