@@ -70,10 +70,9 @@ typedef enum {
 /* Arithmetic of the two contractions a.B and d.B^T (and of E^T D in the core
  * phase).  Factor and core matrices always stay float32 masters; the
  * accumulators are float32 in every mode (Sec. 4.1 uses FP16 inputs with
- * tensor cores).  FT_FP32 is FP32-accurate: the factor phase multiplies on
- * the CUDA cores, the core phase on the tensor cores with three-pass TF32
- * (each operand split into a TF32 head and tail, x = hi + lo, and the
- * product taken as lo.hi + hi.lo + hi.hi).  FT_TF32 and FT_BF16 round the
+ * tensor cores).  FT_FP32 is FP32-accurate: both phases multiply on the
+ * tensor cores with three-pass TF32 (each operand split into a TF32 head and
+ * tail, x = hi + lo, and the product taken as lo.hi + hi.lo + hi.hi).  FT_TF32 and FT_BF16 round the
  * inputs of every contraction to TF32 or BF16 (tensor cores).  Predictions
  * and test errors are FP32-accurate in every mode.  An FT_BF16 context also
  * keeps BF16 copies of the factor rows in its workspace (sum_n I_n * K * 2

@@ -472,8 +472,10 @@ ft_status make_plan(int N, const int64_t *I, const int *J, int R, int64_t nnz, c
   // without the cache the warp-tile pass runs 256-thread CTAs
   if (p->hot_cap == 0) p->factor_threads = 256;
   const int ft_threads = tc ? 256 : p->factor_threads;
-  const int occ_f = std::min(occupancy(p->ks.factor, ft_threads, tc ? p->ks.factor_smem : p->factor_smem),
-                             occupancy(p->ks.factor_fast, ft_threads, tc ? p->ks.factor_smem : p->factor_smem));
+  const int occ_f = std::min({occupancy(p->ks.factor, ft_threads, tc ? p->ks.factor_smem : p->factor_smem),
+                              occupancy(p->ks.factor_fast, ft_threads, tc ? p->ks.factor_smem : p->factor_smem),
+                              occupancy(p->ks.factor_fast_narrow, ft_threads,
+                                        tc ? p->ks.factor_smem : p->factor_smem)});
   const int occ_d = occupancy(p->ks.factor_delta, 256, p->ks.factor_smem);
   const bool store = c.core_scheme == FT_CORE_STORE;
   p->core_fn = store ? p->ks.core_store : p->ks.core;
@@ -945,8 +947,10 @@ ft_status ft_epoch_factors(ft_ctx *c, float lr_a, float lambda_a, const float *c
     if (p.cfg.engine == FT_ENGINE_TCGEN05)
       return launch(c, fast ? p.ks.factor_tc_async : p.ks.factor_tc, p.grid_factor_tc, p.ks.factor_tc_threads,
                     c->hot_active ? p.factor_smem : p.ks.factor_tc_smem, &a, st);
-    return launch(c, fast ? p.ks.factor_fast : p.ks.factor, p.grid_factor, p.factor_threads,
-                  c->hot_active ? p.factor_smem : p.ks.factor_smem, &a, st);
+    // rows read as 16-byte groups in every mode, some narrower than K
+    const bool narrow = !fast && c->hot_active && !scaled && c->vec4mask == (1u << p.N) - 1u;
+    return launch(c, fast ? p.ks.factor_fast : (narrow ? p.ks.factor_fast_narrow : p.ks.factor), p.grid_factor,
+                  p.factor_threads, c->hot_active ? p.factor_smem : p.ks.factor_smem, &a, st);
   }
 
   a.delta = ws_ptr<float>(c, p.off_delta);

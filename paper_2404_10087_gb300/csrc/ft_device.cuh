@@ -782,10 +782,19 @@ __device__ __forceinline__ void factor_tile(const EpochArgs &p, const float *tab
 // access), the hot-row cache on, one step size for every row - with the same
 // rule and no data-dependent branches: a masked nonzero (past the end, or with
 // a coordinate outside its range) reads row 0 of global memory, uses zeros,
-// and skips its stores by predication.  The update is written
-//   a <- (1 - lr lam) a + (lr e) P,
-// the same step as a + lr (e P - lam a) up to rounding.
-template <int N, int K, int MATH>
+// and skips its stores by predication.  The update is the step of
+// a + lr (e P - lam a), written for FP32-accurate products as
+//   a <- a + ((lr e) P + (-lr lam) a)
+// (the step is formed first, so the row is rounded once, by the final add),
+// and for TF32/BF16 products, whose rounding (2^-11, 2^-8 of the products)
+// dwarfs a few float32 roundings of the row, as the two operations
+//   a <- (1 - lr lam) a + (lr e) P.
+// NARROW: rows J_n < K wide (J_n a multiple of 4, 16-byte aligned base): the
+// global rows have stride J_n and only the 4-column groups inside the row are
+// read and written; cached rows stay K wide (zeros past J_n, and the products
+// leave them zero).  Without the cache (rep null) every coordinate is a
+// global row.
+template <int N, int K, int MATH, bool NARROW = false>
 __device__ __forceinline__ void factor_tile_fast(const EpochArgs &p, const float *tabs, float *rep,
                                                  unsigned char *dirty, const TileCoords<N> &tc, int lane) {
   constexpr int CPL = K / 4;
@@ -825,10 +834,12 @@ __device__ __forceinline__ void factor_tile_fast(const EpochArgs &p, const float
   for (int n = 0; n < N; ++n)
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
-      const float *src = hot[n][h] ? rep + r[n][h] * K + CPL * t : p.A[n] + size_t(r[n][h]) * K + CPL * t;
+      const size_t stride = NARROW ? size_t(p.J[n]) : size_t(K);
+      const float *src = hot[n][h] ? rep + r[n][h] * K + CPL * t : p.A[n] + size_t(r[n][h]) * stride + CPL * t;
 #pragma unroll
       for (int w = 0; w < CPL; w += 4) {
-        const float4 f4 = *reinterpret_cast<const float4 *>(src + w);
+        float4 f4 = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (!NARROW || hot[n][h] || CPL * t + w < p.J[n]) f4 = *reinterpret_cast<const float4 *>(src + w);
         f.a[n][h][w] = f.valid[h] ? f4.x : 0.f;
         f.a[n][h][w + 1] = f.valid[h] ? f4.y : 0.f;
         f.a[n][h][w + 2] = f.valid[h] ? f4.z : 0.f;
@@ -839,6 +850,8 @@ __device__ __forceinline__ void factor_tile_fast(const EpochArgs &p, const float
   const float e[2] = {f.x[0] - f.xhat[0], f.x[1] - f.xhat[1]};
   const bool nonfinite = (f.valid[0] && !isfinite(e[0])) || (f.valid[1] && !isfinite(e[1]));
   if (__any_sync(FULL, nonfinite) && lane == 0) atomicOr(p.err, ERRBIT_NONFINITE);
+  constexpr bool ROUND_ONCE = MATH == MATH_FP32 || MATH == MATH_TF32X3;
+  const float nl = -p.lr * p.lam;
   const float keep = 1.f - p.lr * p.lam;
   const float ge[2] = {p.lr * e[0], p.lr * e[1]};
 #pragma unroll
@@ -848,14 +861,23 @@ __device__ __forceinline__ void factor_tile_fast(const EpochArgs &p, const float
     Prod<K, MATH>::run(d, tabs + (N + n) * TW, pp, lane);
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
-      float *dst = hot[n][h] ? rep + r[n][h] * K + CPL * t : p.A[n] + size_t(r[n][h]) * K + CPL * t;
+      const size_t stride = NARROW ? size_t(p.J[n]) : size_t(K);
+      float *dst = hot[n][h] ? rep + r[n][h] * K + CPL * t : p.A[n] + size_t(r[n][h]) * stride + CPL * t;
 #pragma unroll
       for (int w = 0; w < CPL; w += 4) {
-        const float4 o = make_float4(fmaf(ge[h], pp[h][w], keep * f.a[n][h][w]),
-                                     fmaf(ge[h], pp[h][w + 1], keep * f.a[n][h][w + 1]),
-                                     fmaf(ge[h], pp[h][w + 2], keep * f.a[n][h][w + 2]),
-                                     fmaf(ge[h], pp[h][w + 3], keep * f.a[n][h][w + 3]));
-        if (f.valid[h]) *reinterpret_cast<float4 *>(dst + w) = o;
+        float4 o;
+        if constexpr (ROUND_ONCE)
+          o = make_float4(f.a[n][h][w] + fmaf(ge[h], pp[h][w], nl * f.a[n][h][w]),
+                          f.a[n][h][w + 1] + fmaf(ge[h], pp[h][w + 1], nl * f.a[n][h][w + 1]),
+                          f.a[n][h][w + 2] + fmaf(ge[h], pp[h][w + 2], nl * f.a[n][h][w + 2]),
+                          f.a[n][h][w + 3] + fmaf(ge[h], pp[h][w + 3], nl * f.a[n][h][w + 3]));
+        else
+          o = make_float4(fmaf(ge[h], pp[h][w], keep * f.a[n][h][w]),
+                          fmaf(ge[h], pp[h][w + 1], keep * f.a[n][h][w + 1]),
+                          fmaf(ge[h], pp[h][w + 2], keep * f.a[n][h][w + 2]),
+                          fmaf(ge[h], pp[h][w + 3], keep * f.a[n][h][w + 3]));
+        if (f.valid[h] && (!NARROW || hot[n][h] || CPL * t + w < p.J[n]))
+          *reinterpret_cast<float4 *>(dst + w) = o;
       }
       if (hot[n][h] && t == 0) dirty[r[n][h]] = 1;
     }
@@ -884,7 +906,9 @@ __device__ __forceinline__ void factor_tile_fast(const EpochArgs &p, const float
 // DELTA = true: the per-nonzero step is written to p.delta for the
 // deterministic batch reduction; A is not modified.
 // FAST (Hogwild with the hot-row cache, every mode full width, one step size
-// for every row): the tiles run factor_tile_fast.
+// for every row): the tiles run factor_tile_fast; FAST and NARROW: the same
+// where every mode's rows are read as 16-byte groups but some are narrower
+// than K.
 //
 // CTA shape: where the tile fits in 128 registers (K = 16, N <= 3) the
 // cached Hogwild pass runs one 512-thread CTA per SM, so the SM's shared
@@ -897,7 +921,7 @@ struct FactorLaunch {
   static constexpr int THREADS = (K == 16 && N <= 3) ? 512 : 256;
 };
 
-template <int N, int K, int MATH, bool DELTA, bool FAST = false>
+template <int N, int K, int MATH, bool DELTA, bool FAST = false, bool NARROW = false>
 __global__ void __launch_bounds__(FactorLaunch<N, K, MATH>::THREADS) k_factor(const EpochArgs p) {
   extern __shared__ __align__(16) float smem[];
   using L = FactorSmem<N, K, MATH>;
@@ -941,7 +965,7 @@ __global__ void __launch_bounds__(FactorLaunch<N, K, MATH>::THREADS) k_factor(co
     const int64_t cn = c + G;
     if (cn < nct) nxt.load(p, p.begin + (cn * wpc + wid) * FT_TILE, lane, true);
     if (c * wpc + wid < ntiles) {
-      if constexpr (FAST) factor_tile_fast<N, K, MATH>(p, smem, rep, dirty, cur, lane);
+      if constexpr (FAST) factor_tile_fast<N, K, MATH, NARROW>(p, smem, rep, dirty, cur, lane);
       else factor_tile<N, K, MATH, false>(p, smem, rep, dirty, cur, lane);
     }
     cur = nxt;
@@ -1475,10 +1499,15 @@ __global__ void __launch_bounds__(256) k_batch_factor(const BatchArgs b) {
       __syncthreads();
       cur = un.tensor;
     }
+    // the branch-free tile (without a cache) where every mode's rows are read
+    // as 16-byte groups (full width or narrower than K; one variant for both
+    // keeps the registers of the persistent kernel down)
+    const bool groups = ea.vec4mask == (1u << N) - 1u;
     for (int64_t tile = un.tile_begin + wid; tile < un.tile_end; tile += wpc) {
       TileCoords<N> tc;
       tc.load(ea, ea.begin + tile * FT_TILE, lane, true);
-      factor_tile<N, K, MATH, false>(ea, smem, nullptr, nullptr, tc, lane);
+      if (groups) factor_tile_fast<N, K, MATH, true>(ea, smem, nullptr, nullptr, tc, lane);
+      else factor_tile<N, K, MATH, false>(ea, smem, nullptr, nullptr, tc, lane);
     }
   }
 }

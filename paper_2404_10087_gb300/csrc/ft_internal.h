@@ -12,6 +12,7 @@ struct KernelSet {
   // the same pass with the hot-row cache, every mode full width and one step
   // size for every row (the tile without data-dependent branches)
   const void *factor_fast = nullptr;
+  const void *factor_fast_narrow = nullptr;
   const void *factor_delta = nullptr;  // deterministic factor pass (writes per-nonzero steps)
   const void *core = nullptr;          // core-gradient pass
   // the same pass without the BF16 row copies of the workspace (gathers the

@@ -600,7 +600,8 @@ __device__ __forceinline__ void tile_async(const EpochArgs &p, unsigned char *sm
   }
   fence_after();
 
-  // a <- (1 - lr lam) a + (lr e) P, to the cache or to global memory
+  // a <- (1 - lr lam) a + (lr e) P, to the cache or to global memory (the
+  // BF16 products' rounding dwarfs the row's float32 roundings)
   const float keep = 1.f - p.lr * p.lam;
 #pragma unroll
   for (int n = 0; n < N; ++n) {

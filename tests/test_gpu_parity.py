@@ -631,13 +631,15 @@ def test_nonfinite_residual_is_latched():
 
 
 @pytest.mark.parametrize("precision", ["fp32", "bf16"])
-def test_fast_tile_reports_bad_coordinates_and_nonfinite(precision):
-    """The branch-free Hogwild tile (every mode full width, hot-row cache on,
-    one step size) masks a coordinate outside its range (FT_ERR_INDEX) and
+@pytest.mark.parametrize("J", [(16, 16, 16), (8, 12, 4)], ids=["full_width", "narrow"])
+def test_fast_tile_reports_bad_coordinates_and_nonfinite(precision, J):
+    """The branch-free Hogwild tile (every mode full width, or every mode's
+    rows a multiple of 4 wide and some narrower than K; hot-row cache on, one
+    step size) masks a coordinate outside its range (FT_ERR_INDEX) and
     latches a non-finite residual (FT_ERR_NONFINITE); rows of the masked
     nonzero are not written, and the next clean epoch clears the latch."""
     nnz = 16 * 30 + 7
-    I, J, R = (nnz + 3, nnz + 5, nnz + 1), (16, 16, 16), 16
+    I, R = (nnz + 3, nnz + 5, nnz + 1), 16
     g = torch.Generator().manual_seed(17)
     idx = torch.stack([torch.randperm(In, generator=g)[:nnz] for In in I]).to(torch.int32)
     _, x, A, B = synth.random_problem(17, I, J, R, nnz)
