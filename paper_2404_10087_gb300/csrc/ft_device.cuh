@@ -237,9 +237,18 @@ struct Prod<K, MATH_TF32X3> {
   static constexpr int NT = K / 8;
   static constexpr int KS = K / 8;
   static constexpr int WORDS = NT * KS * 32 * 4;
+  // x = hi + lo, each rounded to the 10 stored mantissa bits of TF32 to
+  // nearest, ties away from zero (the rounding of cvt.rna.tf32.f32): adding
+  // half a TF32 ulp (bit 12) to the bit pattern carries into the kept bits
+  // exactly when the 13 dropped bits are at least half an ulp, and clearing
+  // them truncates.  Two integer operations instead of the conversion's
+  // longer sequence (the split is on the inner loops of every FP32-accurate
+  // product).  For finite x below the float32 maximum the bits equal those of
+  // cvt.rna; v - hi is exact in float32.
+  __device__ static uint32_t round_bits(float v) { return (__float_as_uint(v) + 0x1000u) & 0xffffe000u; }
   __device__ static void split(float v, uint32_t &hi, uint32_t &lo) {
-    hi = to_tf32(v);
-    lo = to_tf32(v - __uint_as_float(hi));
+    hi = round_bits(v);
+    lo = round_bits(v - __uint_as_float(hi));
   }
   __device__ static void fill(float *tabf, const float *__restrict__ Bn, int J, int R, int which) {
     uint32_t *tab = reinterpret_cast<uint32_t *>(tabf);

@@ -6,6 +6,9 @@
 #if FT_K == 16 && FT_MATH == 2
 #include "ft_tc05.cuh"
 #endif
+#if FT_K == 16 && FT_MATH == 0
+#include "ft_core32.cuh"
+#endif
 
 #ifndef FT_K
 #error "FT_K must be defined (16 or 32)"
@@ -64,6 +67,17 @@ ft::KernelSet make_set() {
   s.core_store = reinterpret_cast<const void *>(&ft::k_core<N, FT_K, FT_KMATH, true>);
   s.core_store_smem = ft::CoreSmem<N, FT_K, FT_KMATH>::bytes();
   s.core_store_threads = 32 * ft::CoreSmem<N, FT_K, FT_KMATH>::WARPS;
+#endif
+#if FT_K == 16 && FT_MATH == 0
+  // FP32 at K = 16, N <= 5: the CTA-cooperative FP32-accurate core pass
+  if constexpr (N <= 5) {
+    s.core = reinterpret_cast<const void *>(&ft::k_core32<N>);
+    s.core_smem = ft::Core32<N>::bytes();
+    s.core_threads = 32 * ft::Core32<N>::WARPS;
+    s.batch_core = reinterpret_cast<const void *>(&ft::k_batch_core32<N>);
+    s.batch_core_smem = ft::Core32<N>::bytes();
+    s.batch_core_threads = 32 * ft::Core32<N>::WARPS;
+  }
 #endif
 #if FT_MATH == 2
   // BF16: the CTA-cooperative core pass on the BF16 row copies; the caller
