@@ -6,7 +6,7 @@
 #if FT_K == 16 && FT_MATH == 2
 #include "ft_tc05.cuh"
 #endif
-#if FT_K == 16 && FT_MATH == 0
+#if FT_MATH == 0
 #include "ft_core32.cuh"
 #endif
 
@@ -68,15 +68,16 @@ ft::KernelSet make_set() {
   s.core_store_smem = ft::CoreSmem<N, FT_K, FT_KMATH>::bytes();
   s.core_store_threads = 32 * ft::CoreSmem<N, FT_K, FT_KMATH>::WARPS;
 #endif
-#if FT_K == 16 && FT_MATH == 0
-  // FP32 at K = 16, N <= 5: the CTA-cooperative FP32-accurate core pass
-  if constexpr (N <= 5) {
-    s.core = reinterpret_cast<const void *>(&ft::k_core32<N>);
-    s.core_smem = ft::Core32<N>::bytes();
-    s.core_threads = 32 * ft::Core32<N>::WARPS;
-    s.batch_core = reinterpret_cast<const void *>(&ft::k_batch_core32<N>);
-    s.batch_core_smem = ft::Core32<N>::bytes();
-    s.batch_core_threads = 32 * ft::Core32<N>::WARPS;
+#if FT_MATH == 0
+  // FP32 at K = 16 with N <= 5 and at K = 32 with N <= 4: the CTA-cooperative
+  // FP32-accurate core pass
+  if constexpr ((FT_K == 16 && N <= 5) || (FT_K == 32 && N <= 4)) {
+    s.core = reinterpret_cast<const void *>(&ft::k_core32<N, FT_K>);
+    s.core_smem = ft::Core32<N, FT_K>::bytes();
+    s.core_threads = 32 * ft::Core32<N, FT_K>::WARPS;
+    s.batch_core = reinterpret_cast<const void *>(&ft::k_batch_core32<N, FT_K>);
+    s.batch_core_smem = ft::Core32<N, FT_K>::bytes();
+    s.batch_core_threads = 32 * ft::Core32<N, FT_K>::WARPS;
   }
 #endif
 #if FT_MATH == 2
