@@ -1220,8 +1220,12 @@ struct CoopProd {
 template <int N, int K>
 struct CoopSmem {
   // 4-warp CTAs (64-nonzero tiles, six per SM) at K = 16, N <= 3: shorter
-  // barriers, measured 1% faster than 8-warp CTAs; 8 warps elsewhere
-  static constexpr int WARPS = (K == 16 && N <= 3) ? 4 : 8;
+  // barriers, measured 1% faster than 8-warp CTAs.  16 warps at K = 32,
+  // N = 4: one output block per warp (16 blocks), so each warp keeps one
+  // block's compensated sums, which brings the pass to 128 registers and
+  // 16 warps per SM (measured 25.6 -> 22.1 ms on the order-4 tensor; 12
+  // warps: 22.9 ms).  8 warps elsewhere.
+  static constexpr int WARPS = (K == 16 && N <= 3) ? 4 : (K == 32 && N == 4) ? 16 : 8;
   static constexpr int ROWS = WARPS * FT_TILE;              // nonzeros per CTA tile
   static constexpr int LDB = 2 * K + 16;                    // bytes per staged row (conflict-free ldmatrix)
   static constexpr int BUF = ROWS * LDB;                    // bytes of one [ROWS][K] bf16 buffer
