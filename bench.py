@@ -534,28 +534,34 @@ def run_sweep(args, local_rank):
     peak, peak_kind = peak_hbm()
     rows = []
     if args.sweep in ("orders", "all"):
-        # the synthetic orders share one factor step, small enough that no
-        # order diverges (the Netflix-shaped step 0.04 diverged at high order:
-        # every row there meets 1e4 nonzeros per epoch)
+        # the synthetic orders take the largest of three factor steps whose run
+        # stays finite (the Netflix-shaped step 0.04 diverged at high order,
+        # and 0.01 from N = 7: every row there meets 9e3 nonzeros per epoch)
         for N in range(3, 11):
             w = synth.synthetic_order(N, nnz=args.nnz or 100_000_000)
-            w_, tri, trx, tei, tex, A, B = make_workload(dev, None, w)
+            w_, tri, trx, tei, tex, A0, B0 = make_workload(dev, None, w)
             eng = engine_for(args, N, 16, 16)
-            m = ft.FastTuckerPlus(tri, trx, A, B, precision=args.precision, hot_rows=args.hot_rows,
-                                  hot_window=args.hot_window, engine=eng)
-            f, c = time_phases(m, args.steps, args.warmup, stream, lr=LR_ORDERS)
+            # the largest of LR_ORDERS / 1, 3, 10 whose run stays finite
+            for lr in (LR_ORDERS, LR_ORDERS / 3, LR_ORDERS / 10):
+                A = [a.clone() for a in A0]
+                B = [b.clone() for b in B0]
+                m = ft.FastTuckerPlus(tri, trx, A, B, precision=args.precision, hot_rows=args.hot_rows,
+                                      hot_window=args.hot_window, engine=eng)
+                f, c = time_phases(m, args.steps, args.warmup, stream, lr=lr)
+                try:
+                    rmse = m.rmse(tei, tex)[0]
+                except ft.FtError:
+                    rmse = "diverged"
+                m.close()
+                if rmse != "diverged":
+                    break
             nnz = int(trx.numel())
-            try:
-                rmse = m.rmse(tei, tex)[0]
-            except ft.FtError:
-                rmse = "diverged"
             per = algorithmic_bytes_factor(N, w.J)
             rows.append({"study": "order", "N": N, "I": w.I[0], "J": 16, "R": 16, "engine": eng, "nnz_train": nnz,
-                         "lr_a": LR_ORDERS,
+                         "lr_a": lr,
                          "factor_ms": f, "core_ms": c, "value": nnz / ((f + c) / 1e3),
                          "factor_frac_hbm": per * nnz / (f / 1e3) / 1e9 / peak, "test_rmse": rmse})
-            m.close()
-            del tri, trx, tei, tex, A, B
+            del tri, trx, tei, tex, A, B, A0, B0
             torch.cuda.empty_cache()
     if args.sweep in ("ranks", "all"):
         w0, tri, trx, tei, tex, _, _ = make_workload(dev, args.nnz, args.workload)
