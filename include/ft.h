@@ -298,7 +298,8 @@ ft_status ft_core_grad_noalloc(int N, const int64_t *I, const int *J, int R, int
  * Many independent tensors trained together (each with its own order N,
  * ranks J_n and R, nonzeros and matrices).  Tensors are grouped by kernel
  * class (N, padded rank K); every class runs one persistent factor kernel and
- * one persistent core kernel over fixed-size units of its tensors' tiles, and
+ * one persistent core kernel over fixed-size units of its tensors' tiles (the
+ * units dealt round-robin over the class's tensors), and
  * the whole epoch - the factor pass (Hogwild within each tensor), the core
  * pass and one finalize over all tensors - is captured once as a CUDA graph
  * and replayed by ft_batch_epoch.  The paper treats one tensor at a time

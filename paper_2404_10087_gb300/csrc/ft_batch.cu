@@ -273,6 +273,11 @@ ft_status layout_units(ft_batch *b, cudaStream_t st) {
   int64_t poff = 0, elem = 0;
   for (ClassInfo &c : b->classes) {
     c.unit_first = int64_t(units.size());
+    // units of each tensor (partials of a tensor in consecutive slots), then
+    // dealt round-robin over the class's tensors: CTA b takes units b, b + G,
+    // ..., so at any time the CTAs work on many tensors at once instead of
+    // all on the rows of one
+    std::vector<std::vector<ft::BatchUnit>> per;
     for (int t : c.tensors) {
       const TensorInfo &ti = b->tensors[size_t(t)];
       BatchFinalDesc &fd = fin[size_t(t)];
@@ -286,8 +291,9 @@ ft_status layout_units(ft_batch *b, cudaStream_t st) {
       }
       fd.inv_nnz = ti.nnz > 0 ? float(1.0 / double(ti.nnz)) : 0.f;
       fd.poff = poff;
-      const int64_t per = 2LL * ti.N * ti.K * ti.K;
+      const int64_t pfl = 2LL * ti.N * ti.K * ti.K;
       const int64_t nu = std::max<int64_t>(1, (ti.ntiles + c.unit_tiles - 1) / c.unit_tiles);
+      per.emplace_back();
       for (int64_t k = 0; k < nu; ++k) {
         ft::BatchUnit u;
         u.tensor = t;
@@ -295,10 +301,19 @@ ft_status layout_units(ft_batch *b, cudaStream_t st) {
         u.tile_begin = k * c.unit_tiles;
         u.tile_end = std::min<int64_t>(ti.ntiles, (k + 1) * c.unit_tiles);
         u.poff = poff;
-        poff += per;
-        units.push_back(u);
+        poff += pfl;
+        per.back().push_back(u);
       }
       fd.nunits = int(nu);
+    }
+    for (size_t r = 0;; ++r) {
+      bool any = false;
+      for (const std::vector<ft::BatchUnit> &v : per)
+        if (r < v.size()) {
+          units.push_back(v[r]);
+          any = true;
+        }
+      if (!any) break;
     }
     c.nunits = int64_t(units.size()) - c.unit_first;
   }
