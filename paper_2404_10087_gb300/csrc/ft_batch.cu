@@ -207,7 +207,7 @@ ft_status plan_batch(int nt, const ft_tensor_desc *d, const ft_config *cfg_in, f
       c.N = ti.N;
       c.K = ti.K;
       if (!kernel_set(ti.N, ti.K, cfg->precision, &c.ks)) return FT_ERR_SHAPE;
-      c.occ_factor = occupancy(c.ks.batch_factor, 256, c.ks.factor_smem);
+      c.occ_factor = occupancy(c.ks.batch_factor, c.ks.batch_factor_threads, c.ks.factor_smem);
       c.occ_core = occupancy(c.ks.batch_core, c.ks.batch_core_threads, c.ks.batch_core_smem);
       if (c.occ_factor < 1 || c.occ_core < 1) return FT_ERR_CUDA;
       it = cls_of.emplace(key, int(classes->size())).first;
@@ -385,8 +385,8 @@ ft_status capture(ft_batch *b) {
     ok = ok && cudaStreamWaitEvent(bs, b->forked, 0) == cudaSuccess;
     ft::BatchArgs a = class_args(b, c);
     void *argv[] = {&a};
-    ok = ok && cudaLaunchKernel(c.ks.batch_factor, dim3(class_grid(b, c, false)), dim3(256), argv,
-                                c.ks.factor_smem, bs) == cudaSuccess;
+    ok = ok && cudaLaunchKernel(c.ks.batch_factor, dim3(class_grid(b, c, false)), dim3(c.ks.batch_factor_threads),
+                                argv, c.ks.factor_smem, bs) == cudaSuccess;
     ok = ok && launch_core(b, c, bs) == cudaSuccess;
     ok = ok && cudaEventRecord(b->joined[k], bs) == cudaSuccess;
     ok = ok && cudaStreamWaitEvent(st, b->joined[k], 0) == cudaSuccess;

@@ -56,6 +56,7 @@ ft::KernelSet make_set() {
   s.core_smem = ft::CoreSmem<N, FT_K, FT_KMATH>::bytes();
   s.core_threads = 32 * ft::CoreSmem<N, FT_K, FT_KMATH>::WARPS;
   s.batch_factor = reinterpret_cast<const void *>(&ft::k_batch_factor<N, FT_K, FT_FMATH>);
+  s.batch_factor_threads = ft::BatchFactorLaunch<FT_K>::THREADS;
   s.batch_core = reinterpret_cast<const void *>(&ft::k_batch_core<N, FT_K, FT_KMATH>);
   s.batch_core_smem = ft::CoreSmem<N, FT_K, FT_KMATH>::bytes();
   s.batch_core_threads = 32 * ft::CoreSmem<N, FT_K, FT_KMATH>::WARPS;

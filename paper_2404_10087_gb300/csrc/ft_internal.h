@@ -28,6 +28,7 @@ struct KernelSet {
   int core_store_threads = 256;
   // batched persistent kernels of this class (generic core, shared-memory staging)
   const void *batch_factor = nullptr;
+  int batch_factor_threads = 256;
   const void *batch_core = nullptr;
   size_t batch_core_smem = 0;
   int batch_core_threads = 256;
