@@ -81,10 +81,11 @@ def kernel_digest():
     return h.hexdigest()[:16]
 
 
-def recorded_traffic(precision, workload=WORKLOAD, nnz=None, engine="warp"):
+def recorded_traffic(precision, workload=WORKLOAD, nnz=None, engine="warp", hot_window=None):
     """DRAM bytes per factor launch from the committed ncu summary, if it was
     taken on the current kernel source and on this launch (the default
-    workload at full size, warp-tile engine); else None."""
+    workload at full size, warp-tile engine, the same hot-row write-back
+    window); else None."""
     if workload != WORKLOAD or nnz is not None or engine != "warp":
         return None
     p = os.path.join(ROOT, "profiles", "ncu_factor_netflix_zipf.md")
@@ -93,6 +94,9 @@ def recorded_traffic(precision, workload=WORKLOAD, nnz=None, engine="warp"):
     text = open(p).read()
     m = re.search(r"kernel_source_sha256_16:\s*([0-9a-f]+)", text)
     if not m or m.group(1) != kernel_digest():
+        return None
+    w = re.search(r"hot_window:\s*([0-9]+)", text)
+    if hot_window is not None and (not w or int(w.group(1)) != int(hot_window)):
         return None
     m = re.search(rf"traffic_bytes_per_launch_{precision}:\s*([0-9.eE+]+)", text)
     return float(m.group(1)) if m else None
@@ -440,7 +444,7 @@ def run_ours(args, rank, world, local_rank):
     fac_ms = statistics.mean(f_ms)
     achieved = per_nnz * nnz_train / (fac_ms / 1e3) / 1e9
     peak, peak_kind = peak_hbm()
-    traffic = recorded_traffic(args.precision, args.workload, args.nnz, args.engine)
+    traffic = recorded_traffic(args.precision, args.workload, args.nnz, args.engine, m.cfg.hot_window)
     clocks = clk.summary()
     out = {
         "metric": METRIC,

@@ -118,7 +118,7 @@ typedef struct {
    * N <= 3; for the tcgen05 pass with full-width rows, as many of 96 KB as
    * fit beside its 4 x N x 8 KB row stage), 0 = off. */
   int hot_rows;
-  int hot_window;      /* 1 .. 2^20; default 128 */
+  int hot_window;      /* 1 .. 2^20; default 256 */
   int hot_min_count;   /* >= 1; default 2 */
   /* Kernel family of the Hogwild factor pass: FT_ENGINE_WARP (default) = one
    * warp per 16-nonzero tile with mma.sync products; FT_ENGINE_TCGEN05 = one
@@ -153,7 +153,7 @@ enum { FT_ENGINE_WARP = 0, FT_ENGINE_TCGEN05 = 1 };
 enum { FT_CORE_CALC = 0, FT_CORE_STORE = 1 };
 
 /* Fill *cfg with the defaults: FT_FP32, FT_HOGWILD, det_batch 4096, automatic
- * grid, hot_rows -1, hot_window 128, hot_min_count 2, FT_ENGINE_WARP,
+ * grid, hot_rows -1, hot_window 256, hot_min_count 2, FT_ENGINE_WARP,
  * FT_CORE_CALC, l2_persist 0. */
 void ft_config_default(ft_config *cfg);
 

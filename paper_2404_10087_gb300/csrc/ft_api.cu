@@ -840,7 +840,7 @@ void ft_config_default(ft_config *cfg) {
   cfg->det_batch = 4096;
   cfg->blocks_per_sm = 0;
   cfg->hot_rows = -1;
-  cfg->hot_window = 128;
+  cfg->hot_window = 256;
   cfg->hot_min_count = 2;
 }
 
