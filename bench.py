@@ -538,15 +538,17 @@ def run_sweep(args, local_rank):
     peak, peak_kind = peak_hbm()
     rows = []
     if args.sweep in ("orders", "all"):
-        # the synthetic orders take the largest of three factor steps whose run
+        # the synthetic orders take the largest of five factor steps whose run
         # stays finite (the Netflix-shaped step 0.04 diverged at high order,
-        # and 0.01 from N = 7: every row there meets 9e3 nonzeros per epoch)
+        # 0.01 from N = 7 and 0.001 from N = 8, with or without the hot-row
+        # cache and at FP32 alike: every row there meets 9e3 nonzeros per
+        # epoch, and the step's effect grows with the N - 1 factors of d)
         for N in range(3, 11):
             w = synth.synthetic_order(N, nnz=args.nnz or 100_000_000)
             w_, tri, trx, tei, tex, A0, B0 = make_workload(dev, None, w)
             eng = engine_for(args, N, 16, 16)
-            # the largest of LR_ORDERS / 1, 3, 10 whose run stays finite
-            for lr in (LR_ORDERS, LR_ORDERS / 3, LR_ORDERS / 10):
+            # the largest of LR_ORDERS / 1, 3, 10, 30, 100 whose run stays finite
+            for lr in (LR_ORDERS, LR_ORDERS / 3, LR_ORDERS / 10, LR_ORDERS / 30, LR_ORDERS / 100):
                 A = [a.clone() for a in A0]
                 B = [b.clone() for b in B0]
                 m = ft.FastTuckerPlus(tri, trx, A, B, precision=args.precision, hot_rows=args.hot_rows,
