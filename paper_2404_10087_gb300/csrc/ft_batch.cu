@@ -47,29 +47,39 @@ struct FinalArgs {
 };
 
 // Per-tensor core finalize: G = sum over the tensor's unit partials
-// (compensated, unit order), B <- B - lr_b (G / nnz + lambda_b B)
-// (Algorithm 5, last step).
+// (compensated, in a fixed order), B <- B - lr_b (G / nnz + lambda_b B)
+// (Algorithm 5, last step).  One warp per element: lane l sums the partials
+// of units l, l + 32, ... in order, then a fixed xor tree combines the lanes
+// and lane 0 holds the result - the same order on every run.
 __global__ void k_batch_finalize(const FinalArgs a) {
-  const int64_t tid = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (tid >= a.total) return;
+  const int64_t warp = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (warp >= a.total) return;
   int lo = 0, hi = a.ntensors - 1;
   while (lo < hi) {
     const int mid = (lo + hi + 1) / 2;
-    if (a.d[mid].elem_begin <= tid) lo = mid;
+    if (a.d[mid].elem_begin <= warp) lo = mid;
     else hi = mid - 1;
   }
   const BatchFinalDesc &d = a.d[lo];
-  const int64_t local = tid - d.elem_begin;
+  const int64_t local = warp - d.elem_begin;
   const int KK = d.K * d.K;
   const int n = int(local / KK), j = int((local % KK) / d.K), r = int(local % d.K);
   if (j >= d.J[n] || r >= d.R) return;
   const int64_t stride = 2LL * d.N * KK;
   float s = 0.f, c = 0.f;
-  for (int q = 0; q < d.nunits; ++q) {
-    const float *pp = a.partial + d.poff + q * stride + 2 * local;
-    ft::neumaier_add(s, c, pp[0]);
-    c += pp[1];
+  for (int q = lane; q < d.nunits; q += 32) {
+    const float2 pp = *reinterpret_cast<const float2 *>(a.partial + d.poff + q * stride + 2 * local);
+    ft::neumaier_add(s, c, pp.x);
+    c += pp.y;
   }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const float s2 = __shfl_xor_sync(0xffffffffu, s, o), c2 = __shfl_xor_sync(0xffffffffu, c, o);
+    ft::neumaier_add(s, c, s2);
+    c += c2;
+  }
+  if (lane != 0) return;
   const float G = s + c;
   float *b = d.B[n] + j * d.R + r;
   const float bv = *b;
@@ -401,8 +411,8 @@ ft_status capture(ft_batch *b) {
   f.partial = bws<float>(b, b->L.off_partial);
   f.hyper = bws<float>(b, b->L.off_hyper);
   void *fargv[] = {&f};
-  ok = ok && cudaLaunchKernel(reinterpret_cast<const void *>(&k_batch_finalize), dim3(unsigned((total + 255) / 256)),
-                              dim3(256), fargv, 0, st) == cudaSuccess;
+  ok = ok && cudaLaunchKernel(reinterpret_cast<const void *>(&k_batch_finalize), dim3(unsigned((total + 7) / 8)),
+                              dim3(256), fargv, 0, st) == cudaSuccess;   // one warp per element
   ++kernels;
   cudaGraph_t graph = nullptr;
   const cudaError_t e = cudaStreamEndCapture(st, &graph);

@@ -1469,11 +1469,12 @@ __global__ void __launch_bounds__(256) k_eval(const EpochArgs p) {
 // ===================================================== batched persistent epoch
 // Many independent tensors in one launch per kernel class (N, K, precision).
 // The tiles of every tensor of the class are cut into units of a fixed number
-// of CTA tiles; CTA b takes units b, b + G, b + 2G, ...  A CTA reloads the
-// tensor's arguments and operand tables only when its next unit belongs to
-// another tensor.  The factor pass is Hogwild within each tensor; the core
-// pass writes one compensated partial per unit, reduced per tensor in unit
-// order by k_batch_finalize (reproducible bit for bit).
+// of warp tiles, dealt round-robin over the class's tensors; CTA b takes units
+// b, b + G, b + 2G, ...  A CTA reloads the tensor's arguments and operand
+// tables when its next unit belongs to another tensor.  The factor pass is
+// Hogwild within each tensor; the core pass writes one compensated partial
+// per unit, which k_batch_finalize reduces per tensor in a fixed order
+// (reproducible bit for bit).
 namespace ft {
 
 struct BatchUnit {
