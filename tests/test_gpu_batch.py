@@ -11,8 +11,12 @@ pytestmark = pytest.mark.gpu
 
 DEV = "cuda:0"
 
-# (I, J, R, nnz): uneven orders and ranks over both padded ranks K = 16, 32
+# (I, J, R, nnz): uneven orders and ranks over both padded ranks K = 16, 32;
+# rows read as 16-byte groups (J_n a multiple of 4, full width or narrower than
+# K: the branch-free tile) and element by element (J_n = 5, 6, 7: the generic
+# tile) in one kernel class
 SHAPES = [((40, 50, 60), (16, 16, 16), 16, 16 * 40 + 3),
+          ((30, 35, 40), (5, 6, 7), 9, 16 * 28 + 5),
           ((30, 40), (4, 8), 8, 333),
           ((20, 21, 22, 23), (8, 8, 8, 8), 32, 500),
           ((25, 26, 27, 28, 29), (16, 16, 16, 16, 16), 8, 600),
