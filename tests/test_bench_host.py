@@ -40,3 +40,29 @@ def test_factor_byte_model():
     assert bench.algorithmic_bytes_factor(4, [32] * 4) == 1044
     # the small configuration, J = 4
     assert bench.algorithmic_bytes_factor(3, [4, 4, 4]) == 112
+
+
+def test_workload_recipes_match_the_configurations():
+    """The benchmark's recipes carry the configurations' sizes: the planted
+    small tensor, the Netflix-shaped Zipf(1.1) ratings tensor, the order-4
+    Zipf(1.05) tensor and the 64 batched tensors' ranges."""
+    from paper_2404_10087_gb300 import synth
+    w = synth.WORKLOADS["planted_uniform_1e5"]
+    assert (w.I, w.nnz, w.J, w.R, w.dist, w.noise_std) == (
+        (1000,) * 3, 100_000, (4,) * 3, 4, "uniform", 0.1)
+    w = synth.WORKLOADS["netflix_shaped_zipf_1e8"]
+    assert (w.I, w.nnz, w.J, w.R, w.dist, w.zipf_s, w.ratings, w.test_frac) == (
+        (480_000, 18_000, 2_200), 100_000_000, (16,) * 3, 16, "zipf", 1.1, True, 0.1)
+    w = synth.WORKLOADS["order4_zipf_2e8"]
+    assert (w.I, w.nnz, w.J, w.R, w.dist, w.zipf_s, w.noise_std) == (
+        (1_000_000, 1_000_000, 100_000, 1_000), 200_000_000, (32,) * 4, 32, "zipf", 1.05, 0.05)
+    rec = synth.batched_recipe(64, seed=0)
+    assert len(rec) == 64
+    for w in rec:
+        assert w.N in (3, 4, 5) and 10_000 <= w.nnz <= 1_000_000
+        assert all(1_000 <= In <= 100_000 for In in w.I)
+        assert len(set(w.J)) == 1 and w.J[0] in (4, 8, 16) and w.R in (8, 16, 32)
+        assert w.dist == "uniform" and w.noise_std == 0.1
+    # the draw is seeded: the same recipe again
+    again = synth.batched_recipe(64, seed=0)
+    assert [(w.I, w.nnz, w.J, w.R) for w in again] == [(w.I, w.nnz, w.J, w.R) for w in rec]
